@@ -1,0 +1,411 @@
+"""Benchmark of the 4D SlingBAG hot path on GB300.
+
+Headline (one JSON line on rank 0): ball-sensor-sample contributions per
+second of one forward + FP64 loss/residual + adjoint step on the static
+100k-ball workload (vessel tree in a 30 mm cube, 576 sensors on a 55 mm
+hemisphere, 4096 samples at 40 MHz), inputs resident in HBM, L2 flushed
+before every timed step.  Extra keys: end-to-end through host buffers, the
+dominant kernel's roofline, the FP64 oracle timed on the host cores, and
+4D IR iterations/s (100k balls x 20 frames) batched in a CUDA graph vs plain
+per-frame launches.
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+
+N > 1 runs under torchrun as independent replicas (the path needs no
+exchange at one scene per GPU); value = all ranks' contributions / max time.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "ball-sensor-sample contributions/sec (fwd+adjoint) and 4D IR iterations/sec vs per-frame"
+UNIT = "contributions/s"
+# Algorithmic FP32 operations per contribution (an FMA counts as one
+# operation): forward u-step, u^2, amp*u, FMA-accumulate = 4 (+1 ex2 on the
+# SFU); adjoint u-step, u^2, G*E, *u, S1 add, S3 FMA, (1-tau^2/a^2) FMA, SR FMA
+# = 8 (+1 ex2).  Peak FP32 operations/s = 152 SMs x 128 lanes x max SM clock.
+FWD_OPS = 4
+ADJ_OPS = 8
+SMS = 152
+FP32_LANES = 128
+SM_MAX_MHZ_NOMINAL = 2070.0
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=40)
+    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
+    ap.add_argument("--no-4d", action="store_true", help="skip the 4D IR comparison")
+    ap.add_argument("--no-cpu", action="store_true", help="skip the oracle cpu_baseline leg")
+    ap.add_argument("--steps-4d", type=int, default=3)
+    a = ap.parse_args()
+    a.warmup = max(a.warmup, 3)
+    return a
+
+
+# ---------------------------------------------------------------------------
+# clocks sampled during the timed region
+# ---------------------------------------------------------------------------
+class ClockSampler:
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index: int):
+        self.gpu = gpu_index
+        self.proc = None
+        self.path = None
+
+    def start(self):
+        try:
+            fd, self.path = tempfile.mkstemp(suffix=".csv")
+            os.close(fd)
+            self.fh = open(self.path, "w")
+            self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.gpu), f"--query-gpu={self.FIELDS}",
+                                          "--format=csv,noheader,nounits", "-lms", "100"],
+                                         stdout=self.fh, stderr=subprocess.DEVNULL)
+        except (OSError, FileNotFoundError):
+            self.proc = None
+
+    def stop(self) -> dict:
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        time.sleep(0.25)
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        self.fh.close()
+        sm, smax, power = [], [], []
+        reasons = set()
+        names = ["active", "hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        with open(self.path) as fh:
+            for line in fh:
+                parts = [p.strip() for p in line.split(",")]
+                if len(parts) < 9:
+                    continue
+                try:
+                    sm.append(float(parts[1]))
+                    smax.append(float(parts[2]))
+                    power.append(float(parts[3]))
+                except ValueError:
+                    continue
+                for nm, val in zip(names[1:], parts[5:9]):
+                    if val.lower().startswith("active"):
+                        reasons.add(nm)
+        os.unlink(self.path)
+        if not sm:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["no samples"]}
+        # samples under load: drawing well above the idle floor
+        pmin = min(power)
+        loaded = [s for s, p in zip(sm, power) if p >= pmin + 0.25 * (max(power) - pmin)] or sm
+        return {"sm_mhz": statistics.median(loaded), "sm_max_mhz": max(smax), "reasons": sorted(reasons),
+                "samples": len(sm), "power_w_max": max(power)}
+
+
+# ---------------------------------------------------------------------------
+# distributed helpers (replicas; barrier + max over ranks only)
+# ---------------------------------------------------------------------------
+def dist_setup(args):
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    if world > 1:
+        import torch.distributed as dist
+        backend = "nccl" if args.impl == "ours" else "gloo"
+        dist.init_process_group(backend)
+    return world, rank, local
+
+
+def barrier(world):
+    if world > 1:
+        import torch.distributed as dist
+        dist.barrier()
+
+
+def max_over_ranks(v: float, world: int, device) -> float:
+    if world == 1:
+        return v
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([v], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+# ---------------------------------------------------------------------------
+# CPU baseline: the FP64 oracle on a bounded sample of the same workload
+# ---------------------------------------------------------------------------
+def oracle_sample_step(sc, pick, g):
+    import oracle
+    t0 = time.perf_counter()
+    y, n = oracle.forward(sc.balls, sc.sensors[:, pick], sc.c, sc.fs, sc.t0, sc.n_samples, sc.kappa)
+    t1 = time.perf_counter()
+    oracle.adjoint_state(sc.balls, sc.sensors[:, pick], sc.c, sc.fs, sc.t0, sc.n_samples, sc.kappa, g)
+    t2 = time.perf_counter()
+    return n, t1 - t0, t2 - t1
+
+
+def cpu_baseline(sc, n_sensors_sample=None, seed=0):
+    import oracle
+    rng = np.random.default_rng(seed)
+    k = sc.n_sensors if n_sensors_sample is None else n_sensors_sample
+    pick = np.sort(rng.choice(sc.n_sensors, k, replace=False))
+    g = rng.standard_normal((1, len(pick), sc.n_samples)).astype(np.float32)
+    n, tf, ta = oracle_sample_step(sc, pick, g)
+    return {"value": n / (tf + ta), "unit": UNIT, "cores": oracle.max_threads(), "kind": "oracle",
+            "sample": f"{sc.name}: all {sc.n_balls} balls x {len(pick)} of {sc.n_sensors} sensors x "
+                      f"{sc.n_samples} samples, forward + adjoint in FP64 ({n} contributions, "
+                      f"{tf + ta:.1f} s)"}
+
+
+def run_reference(args):
+    world, rank, local = dist_setup(args)
+    if rank != 0:
+        return 0
+    import oracle
+    import pa_inputs
+    sc = pa_inputs.config_scene(2)
+    rng = np.random.default_rng(1)
+    nsamp = 64  # ~1/9 of the workload per step (about a second on 16 cores)
+    total_n, total_t = 0, 0.0
+    for i in range(args.warmup + args.steps):
+        pick = np.sort(rng.choice(sc.n_sensors, nsamp, replace=False))
+        g = rng.standard_normal((1, nsamp, sc.n_samples)).astype(np.float32)
+        n, tf, ta = oracle_sample_step(sc, pick, g)
+        if i >= args.warmup:
+            total_n += n
+            total_t += tf + ta
+    value = total_n / total_t
+    sample = (f"{sc.name}: all {sc.n_balls} balls x {nsamp} random sensors x {sc.n_samples} samples per step, "
+              f"forward + adjoint in FP64")
+    line = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * total_t / args.steps,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+            "data": "synthetic", "config": {"workload": CONFIG_DESC, "sample": sample},
+            "cpu_baseline": {"value": value, "unit": UNIT, "cores": oracle.max_threads(), "kind": "oracle",
+                             "sample": sample},
+            "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line))
+    return 0
+
+
+CONFIG_DESC = ("static-100k: 100,000-ball synthetic vessel tree (20 branching tubes, radii 0.2-1.5 mm, 30 mm cube), "
+               "a~U(0.1,0.4) mm, p~U(0.2,1.0); 576 sensors on a 55 mm Fibonacci hemisphere; c=1.5 mm/us, 40 MHz, "
+               "4096 samples, kappa=5; forward + FP64 loss/residual + adjoint")
+
+
+# ---------------------------------------------------------------------------
+# our arm
+# ---------------------------------------------------------------------------
+def run_ours(args):
+    import torch
+    world, rank, local = dist_setup(args)
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    import pa_inputs
+    import paper_2412_03898_gb300 as pa
+
+    sc = pa_inputs.config_scene(2)
+    n = sc.n_balls
+    to_dev = lambda a: pa.pad_last(torch.from_numpy(np.ascontiguousarray(a, dtype=np.float32)).to(dev))
+    state = to_dev(sc.balls)[None].contiguous()
+    sensors = torch.from_numpy(sc.sensors).to(dev)
+    geom = pa.Geometry(sensors, sc.c, sc.fs, sc.t0, sc.n_samples, sc.kappa)
+    # measured data: the forward of a perturbed cloud (GT differs from the model)
+    gt = sc.balls.copy()
+    rng = np.random.default_rng(42)
+    gt[4] *= rng.uniform(0.9, 1.1, n).astype(np.float32)
+    gt[:3] += rng.normal(0, 0.01, (3, n)).astype(np.float32)
+    meas = pa.forward(geom, to_dev(gt)[None].contiguous(), n)
+    torch.cuda.synchronize()
+    C = pa.count_contributions(geom, state, n)
+    plan = pa.forward_plan(geom, state, n)
+    fws = torch.empty(max(pa.forward_workspace_size(geom, state, n), 16), dtype=torch.uint8, device=dev)
+    lws = torch.empty(1 << 20, dtype=torch.uint8, device=dev)
+    traces = torch.empty(1, geom.n_sensors, geom.n_samples, device=dev)
+    resid = torch.empty_like(traces)
+    loss = torch.empty(1, dtype=torch.float64, device=dev)
+    gstate = torch.empty_like(state)
+    flush = torch.empty(512 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)
+    stream = torch.cuda.current_stream()
+
+    def step(ev=None):
+        if ev is not None:
+            ev[0].record(stream)
+        pa.forward(geom, state, n, out=traces, workspace=fws)
+        if ev is not None:
+            ev[1].record(stream)
+        pa.residual_loss(traces, meas, want_loss=True, want_resid=True, loss_out=loss, resid_out=resid,
+                         workspace=lws)
+        if ev is not None:
+            ev[2].record(stream)
+        pa.adjoint(geom, resid, state=state, n=n, out=gstate)
+        if ev is not None:
+            ev[3].record(stream)
+
+    for _ in range(args.warmup):
+        step()
+    torch.cuda.synchronize()
+    pa.device_error()
+
+    sampler = ClockSampler(local)
+    sampler.start()
+    time.sleep(0.3)
+    evs = [[torch.cuda.Event(enable_timing=True) for _ in range(4)] for _ in range(args.steps)]
+    barrier(world)
+    torch.cuda.synchronize()
+    for k in range(args.steps):
+        flush.zero_()  # write 512 MB > L2 between timed steps (not timed)
+        step(evs[k])
+    torch.cuda.synchronize()
+    barrier(world)
+    t_fwd = [e[0].elapsed_time(e[1]) for e in evs]
+    t_loss = [e[1].elapsed_time(e[2]) for e in evs]
+    t_adj = [e[2].elapsed_time(e[3]) for e in evs]
+    t_step = [e[0].elapsed_time(e[3]) for e in evs]
+    total_ms = max_over_ranks(sum(t_step), world, dev)
+    ms_per_step = total_ms / args.steps
+    value = world * C * args.steps / (total_ms * 1e-3)
+
+    # end to end through host buffers: inputs H2D from pinned memory, result D2H
+    h_state = state.cpu().pin_memory()
+    h_meas = meas.cpu().pin_memory()
+    h_sens = sensors.cpu().pin_memory()
+    h_loss = torch.empty(1, dtype=torch.float64).pin_memory()
+    h_grad = torch.empty(gstate.shape, dtype=torch.float32).pin_memory()
+    e2e_in = h_state.numel() * 4 + h_meas.numel() * 4 + h_sens.numel() * 4
+    e2e_out = h_loss.numel() * 8 + h_grad.numel() * 4
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e2e_ms = 0.0
+    for k in range(args.steps):
+        flush.zero_()
+        e0.record(stream)
+        state.copy_(h_state, non_blocking=True)
+        meas.copy_(h_meas, non_blocking=True)
+        sensors.copy_(h_sens, non_blocking=True)
+        step()
+        h_loss.copy_(loss, non_blocking=True)
+        h_grad.copy_(gstate, non_blocking=True)
+        e1.record(stream)
+        e1.synchronize()
+        e2e_ms += e0.elapsed_time(e1)
+    e2e_ms = max_over_ranks(e2e_ms, world, dev)
+    pa.device_error()
+
+    ir4d = None
+    if not args.no_4d:
+        ir4d = bench_4d(args, pa, pa_inputs, dev, flush)
+    clocks = sampler.stop()
+
+    fwd_avg = statistics.mean(t_fwd)
+    adj_avg = statistics.mean(t_adj)
+    peak_ops = SMS * FP32_LANES * SM_MAX_MHZ_NOMINAL * 1e6
+    if fwd_avg >= adj_avg:
+        dom, ops, dur = "forward (k_forward + split reduce)", FWD_OPS, fwd_avg
+    else:
+        dom, ops, dur = "adjoint (k_adjoint_static)", ADJ_OPS, adj_avg
+    achieved = C * ops / (dur * 1e-3)
+    launches_per_step = 1 + (1 if plan["n_splits"] > 1 else 0) + 2 + 1
+    line = {
+        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": ms_per_step, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+        "config": {"workload": CONFIG_DESC, "n_balls": n, "n_sensors": geom.n_sensors,
+                   "n_samples": geom.n_samples, "contributions_per_step": C,
+                   "l2": "flushed (512 MB write) before every timed step", "forward_plan": plan,
+                   "parallelism": f"replicas x{world}"},
+        "clocks": clocks,
+        "e2e": {"value": world * C * args.steps / (e2e_ms * 1e-3), "unit": UNIT, "h2d_bytes_per_step": e2e_in,
+                "d2h_bytes_per_step": e2e_out},
+        "gpu_launches": launches_per_step * args.steps,
+        "roofline": {"bound": "alu", "kernel": dom, "achieved": achieved / 1e12, "peak": peak_ops / 1e12,
+                     "unit": "TFLOP/s", "frac": achieved / peak_ops, "traffic": None,
+                     "note": f"FP32 operations (FMA = 1) per contribution: forward {FWD_OPS}, adjoint {ADJ_OPS}; "
+                             f"peak = {SMS} SMs x {FP32_LANES} FP32 lanes x {SM_MAX_MHZ_NOMINAL:.0f} MHz"},
+        "kernels_ms": {"forward": fwd_avg, "loss": statistics.mean(t_loss), "adjoint": adj_avg},
+        "fwd_contrib_per_s": C / (fwd_avg * 1e-3), "adj_contrib_per_s": C / (adj_avg * 1e-3),
+    }
+    if ir4d is not None:
+        line["ir4d"] = ir4d
+    if rank == 0 and world == 1 and not args.no_cpu:
+        line["cpu_baseline"] = cpu_baseline(sc)
+    if rank == 0:
+        print(json.dumps(line))
+    return 0
+
+
+def bench_4d(args, pa, pa_inputs, dev, flush):
+    """4D IR iterations/s on 100k canonical balls x 20 frames (576 sensors,
+    4096 samples): batched + CUDA graph vs plain per-frame launches."""
+    import torch
+    from paper_2412_03898_gb300.ir import GGBallIR, init_deformation
+    sc = pa_inputs.config_scene(3)
+    n = sc.n_balls
+    F = sc.n_frames
+    to_dev = lambda a: pa.pad_last(torch.from_numpy(np.ascontiguousarray(a, dtype=np.float32)).to(dev))
+    sensors = torch.from_numpy(sc.sensors).to(dev)
+    geom = pa.Geometry(sensors, sc.c, sc.fs, sc.t0, sc.n_samples, sc.kappa)
+    gt = to_dev(sc.frames).contiguous()
+    meas = pa.forward(geom, gt, n)
+    t = torch.from_numpy(pa_inputs.frame_times(F)).to(dev)
+    canon = to_dev(sc.balls).contiguous()
+    nb = 65
+    deform = init_deformation(nb, canon.shape[-1], dev, omega_scale=0.02, seed=1)
+    del gt
+    out = {"workload": f"{sc.name}: {n} canonical balls, {F} frames, Nb={nb}, {sc.n_sensors} sensors, "
+                       f"{sc.n_samples} samples", "steps": args.steps_4d}
+    C = pa.count_contributions(geom, pa.deform_balls(canon, deform[0], deform[1], deform[2], t, n), n)
+    out["contributions_per_iter"] = C
+    res = {}
+    for mode in ("batched_graph", "per_frame"):
+        ir = GGBallIR(geom, canon.clone(), deform.clone(), t, meas, n)
+        fn = ir.step_graph if mode == "batched_graph" else ir.step_per_frame
+        for _ in range(2):
+            fn()
+        torch.cuda.synchronize()
+        ev = [torch.cuda.Event(enable_timing=True) for _ in range(2)]
+        ms = 0.0
+        for _ in range(args.steps_4d):
+            flush.zero_()
+            ev[0].record()
+            fn()
+            ev[1].record()
+            ev[1].synchronize()
+            ms += ev[0].elapsed_time(ev[1])
+        pa.device_error()
+        res[mode] = args.steps_4d / (ms * 1e-3)
+        out[f"{mode}_iters_per_s"] = res[mode]
+        out[f"{mode}_launches_per_iter"] = ir.launches_per_step(per_frame=(mode == "per_frame"))
+        out[f"{mode}_loss"] = float(ir.loss.sum().item())
+        del ir
+    out["speedup_batched_vs_per_frame"] = res["batched_graph"] / res["per_frame"]
+    out["contrib_per_s_batched"] = 2 * C * res["batched_graph"]
+    return out
+
+
+def main():
+    args = parse()
+    if args.impl == "reference":
+        return run_reference(args)
+    return run_ours(args)
+
+
+if __name__ == "__main__":
+    sys.exit(main())

@@ -1,0 +1,226 @@
+/*
+ * pa.h -- C ABI of the GB300 (sm_103a) library for the data-parallel hot path
+ * of 4D SlingBAG (arXiv 2412.03898): per-frame Gaussian-basis deformation of
+ * a Gaussian-ball point cloud, photoacoustic forward projection of every ball
+ * into every sensor trace, the L2 data-fidelity loss, and the adjoint back to
+ * ball and deformation parameters.
+ *
+ * Conventions (all entry points)
+ * ------------------------------
+ *  - Units: lengths in mm, times in microseconds, sampling rate in MHz,
+ *    sound speed in mm/us.
+ *  - A ball state has five channels in this order: x, y, z (centre mu),
+ *    a (Gaussian standard deviation, "size" a0) and p (peak initial pressure
+ *    p0) -- the attributes of Sec. 2.1.  Ball arrays are structure-of-arrays
+ *    with a channel stride `stride` (elements), stride >= n and
+ *    stride % 4 == 0, and base pointers 16-byte aligned; elements between n
+ *    and stride are never used but must be readable (the library copies whole
+ *    16-byte granules).
+ *  - Pointers named "device" are CUDA device pointers; "host" pointers are
+ *    host memory.  The caller owns every buffer; the library allocates no
+ *    device memory.  Scratch memory is a caller-provided workspace whose size
+ *    is returned by the matching *_workspace_size query.
+ *  - Every call is asynchronous on the caller's stream (`stream` is a
+ *    cudaStream_t; NULL = legacy default stream) and returns a status code.
+ *    Argument errors are detected on the host before anything is launched
+ *    (PA_ERR_INVALID_ARG).  Data-dependent errors found inside kernels (a
+ *    sensor inside a ball's support, a non-positive basis width, a bounded
+ *    wait that ran out) are recorded in a per-device error word and read back
+ *    by pa_device_error().
+ *  - Outputs are overwritten unless PA_ACCUMULATE is set in `flags`, in which
+ *    case results are added to the existing contents.
+ *
+ * The radiator.  The paper drives its reconstruction with SlingBAG's
+ * differentiable forward model (Sec. 2.2, last paragraph) without printing
+ * its formula.  This library uses the exact solution of the 3D wave equation
+ * for a Gaussian initial pressure p*exp(-|x-mu|^2/(2a^2)) with zero initial
+ * velocity.  At a sensor at distance R from mu, sampled at t_k = t0 + k/fs,
+ *     y[k] += p/(2R) * tau * exp(-tau^2/(2a^2)),   tau = R - c t_k,
+ * on the closed window |tau| <= kappa*a (the "arrival window" of the ball),
+ * the inward-travelling term being below (R/a) exp(-R^2/(2a^2)) of the peak.
+ */
+#ifndef PA_H
+#define PA_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#if defined(__GNUC__) || defined(__clang__)
+#define PA_API __attribute__((visibility("default")))
+#else
+#define PA_API
+#endif
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* Status codes. */
+#define PA_OK 0
+#define PA_ERR_INVALID_ARG 1 /* bad pointer, size, alignment or scalar */
+#define PA_ERR_DOMAIN 2      /* sensor inside a ball's support (R <= kappa a), or sigma_n <= 0 */
+#define PA_ERR_CUDA 3        /* a CUDA runtime call failed (launch, attribute, copy) */
+#define PA_ERR_TIMEOUT 4     /* a bounded wait inside a kernel ran out */
+#define PA_ERR_WORKSPACE 5   /* workspace NULL, misaligned or smaller than required */
+
+/* Flags. */
+#define PA_ACCUMULATE 1u      /* add into the output instead of overwriting it */
+#define PA_PROFILE_UNIFORM 2u /* pa_forward only: uniform ball of radius a (N-pulse
+                                 p tau/(2R) on |tau| <= a), used for analytic tests */
+
+/* Acquisition geometry.  `sensors` is a device array [3][sensor_stride]
+ * (x row, y row, z row) of sensor positions.  Constraints: n_sensors >= 1,
+ * sensor_stride >= n_sensors, c > 0, fs > 0, t0 >= 0, n_samples >= 4 and a
+ * multiple of 4, 1 <= kappa <= 8.  The paper's arrays are sparse 2D arrays
+ * on spheres with Fibonacci layouts (Sec. 3.1, Sec. 3.2). */
+typedef struct pa_geom {
+    const float *sensors;
+    int32_t n_sensors;
+    int32_t sensor_stride;
+    float c;         /* speed of sound, mm/us */
+    float fs;        /* sampling rate, MHz */
+    float t0;        /* time of sample 0, us */
+    int32_t n_samples; /* T */
+    float kappa;     /* window half-width in units of a */
+} pa_geom;
+
+/* Per-frame ball states (Eq. 1 outputs, or a static SlingBAG cloud):
+ * device array [n_frames][5][stride], channels x, y, z, a, p. */
+typedef struct pa_balls {
+    const float *state;
+    int64_t n;
+    int64_t stride;
+} pa_balls;
+
+/* GGBall parameters (Sec. 2.2, Eq. 1-2): canonical cloud `canon`
+ * [5][stride] and, per channel, ball and basis function, the weight omega,
+ * centre theta and width sigma of the Gaussian basis, each device
+ * [5][n_basis][stride].  1 <= n_basis <= 128 (the paper uses 65). */
+typedef struct pa_canon {
+    const float *canon;
+    const float *omega;
+    const float *theta;
+    const float *sigma;
+    int64_t n;
+    int64_t stride;
+    int32_t n_basis;
+} pa_canon;
+
+/* Gradient outputs of pa_adjoint.  Static mode: `state` is
+ * [n_frames][5][stride] = dL/d(per-frame state); omega/theta/sigma unused.
+ * 4D mode: `state` is [5][stride] = dL/d(canonical cloud) and
+ * omega/theta/sigma are [5][n_basis][stride]. */
+typedef struct pa_grads {
+    float *state;
+    float *omega;
+    float *theta;
+    float *sigma;
+} pa_grads;
+
+/* Human-readable name of a status code (static storage). */
+PA_API const char *pa_status_string(int32_t status);
+
+/* Library ABI version (major*100 + minor). */
+PA_API int32_t pa_version(void);
+
+/* Reads, returns in *out (host) and clears the device error word of the
+ * current device.  Synchronises `stream`.  *out is PA_OK or the first
+ * data-dependent error recorded by a kernel since the last call. */
+PA_API int32_t pa_device_error(void *stream, int32_t *out);
+
+/* Eq. 1-2 (Sec. 2.2): deformed state of every ball at every frame,
+ *   q(t_f) = q0 (1 + sum_n omega_n exp(-(t_f - theta_n)^2 / (2 sigma_n^2)))
+ * for q in (x, y, z, a, p), one independent H per channel.
+ *   t_frames  device [n_frames] normalised frame times (t_f = f/(F-1) in the
+ *             paper's reading of "normalized time frame")
+ *   state_out device [n_frames][5][canon->stride]
+ * sigma_n <= 0 records PA_ERR_DOMAIN (that term is skipped). */
+PA_API int32_t pa_deform_balls(const pa_canon *canon, const float *t_frames, int32_t n_frames,
+                        float *state_out, void *stream);
+
+/* Scratch bytes pa_forward needs for this problem (0 if none). */
+PA_API size_t pa_forward_workspace_size(const pa_geom *geom, const pa_balls *balls, int32_t n_frames);
+
+/* Forward projection (Sec. 2.2, last paragraph; Sec. 2.1): for every frame f,
+ * sensor s and sample k, the sum over balls of the radiated pulse above.
+ *   traces    device [n_frames][n_sensors][n_samples], 16-byte aligned
+ *   workspace device scratch of at least pa_forward_workspace_size() bytes,
+ *             256-byte aligned (may be NULL when the size is 0)
+ * Balls with a <= 0 or p == 0 contribute nothing; a pair with R <= kappa a is
+ * skipped and records PA_ERR_DOMAIN.  Deterministic: the same inputs give
+ * bitwise the same traces. */
+PA_API int32_t pa_forward(const pa_geom *geom, const pa_balls *balls, int32_t n_frames, float *traces,
+                   uint32_t flags, void *workspace, size_t workspace_bytes, void *stream);
+
+/* pa_forward with an explicit tile plan, for autotuning.  tiles = {sensors
+ * per CTA (1..32, 0 = default), samples per CTA (multiple of 4, 0 = default),
+ * balls per TMA stage (multiple of 4, 0 = default), ball splits (0 =
+ * default)}, host array, or NULL for the built-in heuristic.  Results are
+ * identical to pa_forward up to float summation order across splits. */
+PA_API size_t pa_forward_workspace_size_ex(const pa_geom *geom, const pa_balls *balls, int32_t n_frames,
+                                           const int32_t *tiles);
+PA_API int32_t pa_forward_ex(const pa_geom *geom, const pa_balls *balls, int32_t n_frames, float *traces,
+                             uint32_t flags, const int32_t *tiles, void *workspace, size_t workspace_bytes,
+                             void *stream);
+
+/* The plan pa_forward_ex would use: out6 (host) receives {sensors per CTA,
+ * samples per CTA, balls per stage, ball splits, CTAs launched, dynamic
+ * shared memory bytes per CTA}. */
+PA_API int32_t pa_forward_plan_info(const pa_geom *geom, const pa_balls *balls, int32_t n_frames,
+                                    const int32_t *tiles, int32_t *out6);
+
+/* Adjoint of pa_forward (gradients of the L2 loss, Sec. 2.2, last paragraph:
+ * all baseline attributes and all (theta, sigma, omega) are learnable).
+ * Given trace_grad = dL/dy, device [n_frames][n_sensors][n_samples], and an
+ * optional per-frame scale (device [n_frames] or NULL = 1) applied to it:
+ *  - static mode (balls != NULL, canon == NULL): grads->state receives
+ *    dL/d(x, y, z, a, p) per frame;
+ *  - 4D mode (balls == NULL, canon != NULL, t_frames device [n_frames]):
+ *    the per-frame state is recomputed from Eq. 1-2 inside the kernel (never
+ *    stored) and the chain rule of Eq. 1-2 gives dL/d(canonical cloud) and
+ *    dL/d(omega, theta, sigma), summed over frames.
+ * Every per-ball gradient is written by exactly one warp: no atomics, and
+ * deterministic.  Inactive balls (a <= 0 or p == 0) get zero state gradient. */
+PA_API int32_t pa_adjoint(const pa_geom *geom, const pa_balls *balls, const pa_canon *canon,
+                   const float *t_frames, int32_t n_frames, const float *trace_grad,
+                   const float *frame_scale, pa_grads *grads, uint32_t flags, void *stream);
+
+/* Scratch bytes pa_residual_loss needs. */
+PA_API size_t pa_loss_workspace_size(int64_t per_frame, int32_t n_frames);
+
+/* L2 data-fidelity loss (Sec. 2.2, last paragraph), per frame, in FP64:
+ *   loss[f]  = sum_i (pred[f][i] - meas[f][i])^2          (device [n_frames], or NULL)
+ *   resid[f][i] = 2 scale[f] (pred[f][i] - meas[f][i])     (device, or NULL)
+ * pred, meas, resid: device [n_frames][per_frame], 16-byte aligned,
+ * per_frame % 4 == 0.  frame_scale: device [n_frames] or NULL (= 1).
+ * Deterministic (fixed reduction order). */
+PA_API int32_t pa_residual_loss(const float *pred, const float *meas, int64_t per_frame, int32_t n_frames,
+                         const float *frame_scale, double *loss, float *resid, void *workspace,
+                         size_t workspace_bytes, void *stream);
+
+/* Sum of squares in FP64 of a device float array (gradient norms), written to
+ * *out (device double).  n % 4 == 0, x 16-byte aligned. */
+PA_API int32_t pa_sumsq(const float *x, int64_t n, double *out, void *workspace, size_t workspace_bytes,
+                 void *stream);
+
+/* Number of (frame, sensor, ball, sample) terms pa_forward sums, written to
+ * *out (device uint64).  This is the "contribution" count of the throughput
+ * metric. */
+PA_API int32_t pa_count_contributions(const pa_geom *geom, const pa_balls *balls, int32_t n_frames,
+                               unsigned long long *out, void *stream);
+
+/* One Adam step on a device float array (the paper's optimiser is not named;
+ * Sec. 3.2 gives per-group learning rates and a step decay):
+ *   m = b1 m + (1-b1) g;  v = b2 v + (1-b2) g^2;
+ *   x -= lr * (m / (1 - b1^step)) / (sqrt(v / (1 - b2^step)) + eps).
+ * x, g, m, v device [n], 16-byte aligned. step >= 1.  The scalars are host
+ * doubles; 1 - b1, 1 - b2 and the bias corrections are formed in double and
+ * rounded once to float. */
+PA_API int32_t pa_adam_step(float *x, const float *g, float *m, float *v, int64_t n, double lr, double beta1,
+                            double beta2, double eps, int32_t step, void *stream);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* PA_H */

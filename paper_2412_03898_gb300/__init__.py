@@ -1,0 +1,343 @@
+"""GB300-native (sm_103a) hot path of 4D SlingBAG (arXiv 2412.03898).
+
+Torch-facing binding of the C ABI in include/pa.h.  Every step of the path
+runs in the library's CUDA kernels; this module only checks tensors, builds
+the argument structs and passes raw device pointers and the current CUDA
+stream.  It raises if libpa.so is missing or a tensor is not on a CUDA
+device: there is no CPU fallback.
+
+Layouts (see include/pa.h): ball states [F, 5, stride] float32 with channels
+(x, y, z, a, p) and stride % 4 == 0; deformation parameters [5, Nb, stride];
+sensors [3, S]; traces [F, S, T].
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+from typing import Optional, Sequence
+
+import torch
+
+from . import _lib
+from ._lib import PAError
+
+__all__ = [
+    "PAError", "Geometry", "round4", "pad_last", "deform_balls", "forward", "adjoint", "residual_loss", "sumsq",
+    "count_contributions", "adam_step", "device_error", "forward_plan", "forward_workspace_size",
+    "PAProject", "PAProject4D", "PALoss",
+]
+
+
+
+def _ensure_built() -> None:
+    """Build libpa.so in-tree when it is missing or older than its sources."""
+    from . import build as _build
+    if os.path.exists(_lib.LIB_PATH) and not _build._stale():
+        return
+    try:
+        _build.build()
+    except (OSError, RuntimeError) as e:
+        if not os.path.exists(_lib.LIB_PATH):
+            raise ImportError(f"libpa.so is missing and could not be built: {e}") from e
+
+
+_ensure_built()
+_LIB = _lib.load()
+
+
+def round4(n: int) -> int:
+    return (int(n) + 3) // 4 * 4
+
+
+def _stream() -> ctypes.c_void_p:
+    return ctypes.c_void_p(torch.cuda.current_stream().cuda_stream)
+
+
+def _ptr(t: Optional[torch.Tensor]) -> Optional[int]:
+    return None if t is None else t.data_ptr()
+
+
+def _check(t: torch.Tensor, name: str, dtype=torch.float32) -> torch.Tensor:
+    if not isinstance(t, torch.Tensor):
+        raise TypeError(f"{name} must be a torch.Tensor")
+    if not t.is_cuda:
+        raise ValueError(f"{name} must be a CUDA tensor (this library has no CPU path)")
+    if t.dtype != dtype:
+        raise TypeError(f"{name} must be {dtype}, got {t.dtype}")
+    if not t.is_contiguous():
+        raise ValueError(f"{name} must be contiguous")
+    return t
+
+
+def pad_last(x: torch.Tensor, stride: Optional[int] = None) -> torch.Tensor:
+    """Copy x [..., N] into a zero-padded contiguous float32 [..., stride]
+    buffer (stride = N rounded up to a multiple of 4 by default)."""
+    n = x.shape[-1]
+    stride = round4(n) if stride is None else int(stride)
+    out = torch.zeros(*x.shape[:-1], stride, dtype=torch.float32, device=x.device)
+    out[..., :n] = x
+    return out
+
+
+class Geometry:
+    """Sensor array and acquisition scalars (pa_geom)."""
+
+    def __init__(self, sensors: torch.Tensor, c: float, fs: float, t0: float, n_samples: int, kappa: float = 5.0):
+        self.sensors = _check(sensors, "sensors")
+        if sensors.dim() != 2 or sensors.shape[0] != 3:
+            raise ValueError("sensors must be [3, S]")
+        self.c, self.fs, self.t0 = float(c), float(fs), float(t0)
+        self.n_samples, self.kappa = int(n_samples), float(kappa)
+        self._struct = _lib.pa_geom(self.sensors.data_ptr(), self.n_sensors, self.n_sensors, self.c, self.fs,
+                                    self.t0, self.n_samples, self.kappa)
+
+    @property
+    def n_sensors(self) -> int:
+        return int(self.sensors.shape[1])
+
+    def struct(self) -> _lib.pa_geom:
+        return self._struct
+
+    def __repr__(self):
+        return (f"Geometry(S={self.n_sensors}, c={self.c}, fs={self.fs}, t0={self.t0}, T={self.n_samples}, "
+                f"kappa={self.kappa})")
+
+
+def _balls_struct(state: torch.Tensor, n: Optional[int]):
+    _check(state, "state")
+    if state.dim() == 2:
+        state = state.unsqueeze(0)
+    if state.dim() != 3 or state.shape[1] != 5:
+        raise ValueError("state must be [F, 5, stride]")
+    stride = int(state.shape[2])
+    n = stride if n is None else int(n)
+    return state, _lib.pa_balls(state.data_ptr(), n, stride), n
+
+
+def _canon_struct(canon, omega, theta, sigma, n):
+    for t, nm in ((canon, "canon"), (omega, "omega"), (theta, "theta"), (sigma, "sigma")):
+        _check(t, nm)
+    stride = int(canon.shape[-1])
+    nb = int(omega.shape[1])
+    if tuple(canon.shape) != (5, stride) or tuple(omega.shape) != (5, nb, stride) or \
+            theta.shape != omega.shape or sigma.shape != omega.shape:
+        raise ValueError("canon must be [5, stride] and omega/theta/sigma [5, Nb, stride]")
+    n = stride if n is None else int(n)
+    return _lib.pa_canon(canon.data_ptr(), omega.data_ptr(), theta.data_ptr(), sigma.data_ptr(), n, stride, nb), n
+
+
+def device_error(raise_on_error: bool = True) -> int:
+    """Read and clear the device error word (synchronises the stream)."""
+    out = ctypes.c_int32(0)
+    _lib.check(_LIB.pa_device_error(_stream(), ctypes.byref(out)), "pa_device_error")
+    if raise_on_error and out.value != 0:
+        raise PAError(out.value, "kernel")
+    return int(out.value)
+
+
+def deform_balls(canon: torch.Tensor, omega: torch.Tensor, theta: torch.Tensor, sigma: torch.Tensor,
+                 t_frames: torch.Tensor, n: Optional[int] = None, out: Optional[torch.Tensor] = None) -> torch.Tensor:
+    """Eq. 1-2: per-frame states [F, 5, stride] from the GGBall parameters."""
+    cs, n = _canon_struct(canon, omega, theta, sigma, n)
+    _check(t_frames, "t_frames")
+    F = int(t_frames.numel())
+    if out is None:
+        out = torch.empty(F, 5, canon.shape[-1], dtype=torch.float32, device=canon.device)
+    _check(out, "out")
+    _lib.check(_LIB.pa_deform_balls(ctypes.byref(cs), t_frames.data_ptr(), F, out.data_ptr(), _stream()),
+               "pa_deform_balls")
+    return out
+
+
+def _tiles(tiles: Optional[Sequence[int]]):
+    if tiles is None:
+        return None
+    arr = (ctypes.c_int32 * 4)(*[int(v) for v in tiles])
+    return arr
+
+
+def forward_workspace_size(geom: Geometry, state: torch.Tensor, n: Optional[int] = None,
+                           tiles: Optional[Sequence[int]] = None) -> int:
+    state, bs, n = _balls_struct(state, n)
+    t = _tiles(tiles)
+    return int(_LIB.pa_forward_workspace_size_ex(ctypes.byref(geom.struct()), ctypes.byref(bs),
+                                                 int(state.shape[0]), t))
+
+
+def forward_plan(geom: Geometry, state: torch.Tensor, n: Optional[int] = None,
+                 tiles: Optional[Sequence[int]] = None) -> dict:
+    state, bs, n = _balls_struct(state, n)
+    out = (ctypes.c_int32 * 6)()
+    _lib.check(_LIB.pa_forward_plan_info(ctypes.byref(geom.struct()), ctypes.byref(bs), int(state.shape[0]),
+                                         _tiles(tiles), out), "pa_forward_plan_info")
+    return dict(s_tile=out[0], t_tile=out[1], nb_tile=out[2], n_splits=out[3], ctas=out[4], smem=out[5])
+
+
+def forward(geom: Geometry, state: torch.Tensor, n: Optional[int] = None, out: Optional[torch.Tensor] = None,
+            accumulate: bool = False, uniform: bool = False, tiles: Optional[Sequence[int]] = None,
+            workspace: Optional[torch.Tensor] = None) -> torch.Tensor:
+    """Forward projection: traces [F, S, T] of the states [F, 5, stride]."""
+    state, bs, n = _balls_struct(state, n)
+    F = int(state.shape[0])
+    if out is None:
+        if accumulate:
+            raise ValueError("accumulate=True needs out")
+        out = torch.empty(F, geom.n_sensors, geom.n_samples, dtype=torch.float32, device=state.device)
+    _check(out, "out")
+    t = _tiles(tiles)
+    need = int(_LIB.pa_forward_workspace_size_ex(ctypes.byref(geom.struct()), ctypes.byref(bs), F, t))
+    if need > 0 and (workspace is None or workspace.numel() < need):
+        workspace = torch.empty(need, dtype=torch.uint8, device=state.device)
+    flags = (_lib.PA_ACCUMULATE if accumulate else 0) | (_lib.PA_PROFILE_UNIFORM if uniform else 0)
+    ws_ptr = workspace.data_ptr() if need > 0 else None
+    ws_n = workspace.numel() if need > 0 else 0
+    _lib.check(_LIB.pa_forward_ex(ctypes.byref(geom.struct()), ctypes.byref(bs), F, out.data_ptr(), flags, t,
+                                  ws_ptr, ws_n, _stream()), "pa_forward")
+    return out
+
+
+def adjoint(geom: Geometry, trace_grad: torch.Tensor, state: Optional[torch.Tensor] = None,
+            n: Optional[int] = None, canon: Optional[torch.Tensor] = None, omega: Optional[torch.Tensor] = None,
+            theta: Optional[torch.Tensor] = None, sigma: Optional[torch.Tensor] = None,
+            t_frames: Optional[torch.Tensor] = None, frame_scale: Optional[torch.Tensor] = None,
+            accumulate: bool = False, out=None):
+    """Adjoint of `forward`.  Static mode (state given): returns dL/dstate
+    [F, 5, stride].  4D mode (canon, omega, theta, sigma, t_frames given):
+    returns (g_canon [5, stride], g_omega, g_theta, g_sigma [5, Nb, stride])."""
+    _check(trace_grad, "trace_grad")
+    F = int(trace_grad.shape[0])
+    if frame_scale is not None:
+        _check(frame_scale, "frame_scale")
+    flags = _lib.PA_ACCUMULATE if accumulate else 0
+    if state is not None:
+        state, bs, n = _balls_struct(state, n)
+        if out is None:
+            out = torch.empty_like(state)
+        grads = _lib.pa_grads(out.data_ptr(), None, None, None)
+        _lib.check(_LIB.pa_adjoint(ctypes.byref(geom.struct()), ctypes.byref(bs), None, None, F,
+                                   trace_grad.data_ptr(), _ptr(frame_scale), ctypes.byref(grads), flags, _stream()),
+                   "pa_adjoint")
+        return out
+    cs, n = _canon_struct(canon, omega, theta, sigma, n)
+    _check(t_frames, "t_frames")
+    if out is None:
+        out = (torch.empty_like(canon), torch.empty_like(omega), torch.empty_like(theta), torch.empty_like(sigma))
+    grads = _lib.pa_grads(*[o.data_ptr() for o in out])
+    _lib.check(_LIB.pa_adjoint(ctypes.byref(geom.struct()), None, ctypes.byref(cs), t_frames.data_ptr(), F,
+                               trace_grad.data_ptr(), _ptr(frame_scale), ctypes.byref(grads), flags, _stream()),
+               "pa_adjoint")
+    return out
+
+
+def residual_loss(pred: torch.Tensor, meas: torch.Tensor, frame_scale: Optional[torch.Tensor] = None,
+                  want_loss: bool = True, want_resid: bool = False, loss_out: Optional[torch.Tensor] = None,
+                  resid_out: Optional[torch.Tensor] = None, workspace: Optional[torch.Tensor] = None):
+    """Per-frame FP64 loss sum (pred-meas)^2 and/or residual 2 scale (pred-meas)."""
+    _check(pred, "pred")
+    _check(meas, "meas")
+    F = int(pred.shape[0])
+    per = int(pred.numel() // max(F, 1))
+    loss = None
+    if want_loss:
+        loss = loss_out if loss_out is not None else torch.empty(F, dtype=torch.float64, device=pred.device)
+        _check(loss, "loss", torch.float64)
+    resid = None
+    if want_resid:
+        resid = resid_out if resid_out is not None else torch.empty_like(pred)
+        _check(resid, "resid")
+    need = int(_LIB.pa_loss_workspace_size(per, F))
+    if workspace is None or workspace.numel() < need:
+        workspace = torch.empty(max(need, 16), dtype=torch.uint8, device=pred.device)
+    _lib.check(_LIB.pa_residual_loss(pred.data_ptr(), meas.data_ptr(), per, F, _ptr(frame_scale), _ptr(loss),
+                                     _ptr(resid), workspace.data_ptr(), workspace.numel(), _stream()),
+               "pa_residual_loss")
+    return loss, resid
+
+
+def sumsq(x: torch.Tensor, out: Optional[torch.Tensor] = None) -> torch.Tensor:
+    """FP64 sum of squares of a float32 CUDA tensor (gradient norms)."""
+    _check(x, "x")
+    out = out if out is not None else torch.empty(1, dtype=torch.float64, device=x.device)
+    need = int(_LIB.pa_loss_workspace_size(x.numel(), 1))
+    ws = torch.empty(max(need, 16), dtype=torch.uint8, device=x.device)
+    _lib.check(_LIB.pa_sumsq(x.data_ptr(), x.numel(), out.data_ptr(), ws.data_ptr(), ws.numel(), _stream()),
+               "pa_sumsq")
+    return out
+
+
+def count_contributions(geom: Geometry, state: torch.Tensor, n: Optional[int] = None) -> int:
+    """Number of (frame, sensor, ball, sample) terms the forward sums."""
+    state, bs, n = _balls_struct(state, n)
+    out = torch.zeros(1, dtype=torch.int64, device=state.device)
+    _lib.check(_LIB.pa_count_contributions(ctypes.byref(geom.struct()), ctypes.byref(bs), int(state.shape[0]),
+                                           out.data_ptr(), _stream()), "pa_count_contributions")
+    return int(out.item())
+
+
+def adam_step(x: torch.Tensor, g: torch.Tensor, m: torch.Tensor, v: torch.Tensor, lr: float, step: int,
+              beta1: float = 0.9, beta2: float = 0.999, eps: float = 1e-8) -> None:
+    for t, nm in ((x, "x"), (g, "g"), (m, "m"), (v, "v")):
+        _check(t, nm)
+    _lib.check(_LIB.pa_adam_step(x.data_ptr(), g.data_ptr(), m.data_ptr(), v.data_ptr(), x.numel(), float(lr),
+                                 float(beta1), float(beta2), float(eps), int(step), _stream()), "pa_adam_step")
+
+
+# ---------------------------------------------------------------------------
+# Autograd wrappers (the differentiation pattern: forward and adjoint as one
+# torch.autograd.Function; 4D states are recomputed in backward, not stored).
+# ---------------------------------------------------------------------------
+
+class PAProject(torch.autograd.Function):
+    """states [F, 5, stride] -> traces [F, S, T]."""
+
+    @staticmethod
+    def forward(ctx, state, geom: Geometry, n: Optional[int] = None):
+        ctx.geom, ctx.n = geom, n
+        ctx.save_for_backward(state)
+        return forward(geom, state, n)
+
+    @staticmethod
+    def backward(ctx, g):
+        (state,) = ctx.saved_tensors
+        gs = adjoint(ctx.geom, g.contiguous(), state=state, n=ctx.n)
+        return gs, None, None
+
+
+class PAProject4D(torch.autograd.Function):
+    """(canon, omega, theta, sigma) -> traces [F, S, T] through Eq. 1-2.  The
+    per-frame states live only for the forward call; backward recomputes them
+    inside the adjoint kernel."""
+
+    @staticmethod
+    def forward(ctx, canon, omega, theta, sigma, geom: Geometry, t_frames, n: Optional[int] = None):
+        state = deform_balls(canon, omega, theta, sigma, t_frames, n)
+        traces = forward(geom, state, n)
+        del state
+        ctx.geom, ctx.n = geom, n
+        ctx.save_for_backward(canon, omega, theta, sigma, t_frames)
+        return traces
+
+    @staticmethod
+    def backward(ctx, g):
+        canon, omega, theta, sigma, t_frames = ctx.saved_tensors
+        gc, go, gt, gs = adjoint(ctx.geom, g.contiguous(), canon=canon, omega=omega, theta=theta, sigma=sigma,
+                                 t_frames=t_frames, n=ctx.n)
+        return gc, go, gt, gs, None, None, None
+
+
+class PALoss(torch.autograd.Function):
+    """(pred, meas) [F, S, T] -> per-frame FP64 loss [F]."""
+
+    @staticmethod
+    def forward(ctx, pred, meas):
+        loss, _ = residual_loss(pred, meas, want_loss=True)
+        ctx.save_for_backward(pred, meas)
+        return loss
+
+    @staticmethod
+    def backward(ctx, gl):
+        pred, meas = ctx.saved_tensors
+        scale = gl.to(torch.float32).contiguous()
+        _, resid = residual_loss(pred, meas, frame_scale=scale, want_loss=False, want_resid=True)
+        gm = -resid if ctx.needs_input_grad[1] else None
+        return resid, gm

@@ -1,0 +1,110 @@
+"""ctypes declarations of the C ABI in include/pa.h (libpa.so, built in-tree).
+
+Argument marshalling only.  Importing this module loads the CUDA library and
+raises if it is missing: there is no CPU fallback.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(HERE, "libpa.so")
+
+PA_OK = 0
+PA_ERR_INVALID_ARG = 1
+PA_ERR_DOMAIN = 2
+PA_ERR_CUDA = 3
+PA_ERR_TIMEOUT = 4
+PA_ERR_WORKSPACE = 5
+PA_ACCUMULATE = 1
+PA_PROFILE_UNIFORM = 2
+
+c_float_p = ctypes.c_void_p  # device pointers travel as void*
+
+
+class pa_geom(ctypes.Structure):
+    _fields_ = [("sensors", ctypes.c_void_p), ("n_sensors", ctypes.c_int32), ("sensor_stride", ctypes.c_int32),
+                ("c", ctypes.c_float), ("fs", ctypes.c_float), ("t0", ctypes.c_float),
+                ("n_samples", ctypes.c_int32), ("kappa", ctypes.c_float)]
+
+
+class pa_balls(ctypes.Structure):
+    _fields_ = [("state", ctypes.c_void_p), ("n", ctypes.c_int64), ("stride", ctypes.c_int64)]
+
+
+class pa_canon(ctypes.Structure):
+    _fields_ = [("canon", ctypes.c_void_p), ("omega", ctypes.c_void_p), ("theta", ctypes.c_void_p),
+                ("sigma", ctypes.c_void_p), ("n", ctypes.c_int64), ("stride", ctypes.c_int64),
+                ("n_basis", ctypes.c_int32)]
+
+
+class pa_grads(ctypes.Structure):
+    _fields_ = [("state", ctypes.c_void_p), ("omega", ctypes.c_void_p), ("theta", ctypes.c_void_p),
+                ("sigma", ctypes.c_void_p)]
+
+
+class PAError(RuntimeError):
+    def __init__(self, status: int, where: str):
+        self.status = status
+        super().__init__(f"{where}: {status_string(status)}")
+
+
+_lib = None
+
+
+def load() -> ctypes.CDLL:
+    global _lib
+    if _lib is not None:
+        return _lib
+    if not os.path.exists(LIB_PATH):
+        raise ImportError(f"libpa.so not built ({LIB_PATH}); run __graft_entry__.build() or "
+                          "python paper_2412_03898_gb300/build.py")
+    lib = ctypes.CDLL(LIB_PATH)
+    P = ctypes.c_void_p
+    i32, i64, u32, f32, sz = ctypes.c_int32, ctypes.c_int64, ctypes.c_uint32, ctypes.c_float, ctypes.c_size_t
+    G, B, C, GR = (ctypes.POINTER(pa_geom), ctypes.POINTER(pa_balls), ctypes.POINTER(pa_canon),
+                   ctypes.POINTER(pa_grads))
+    I32P = ctypes.POINTER(ctypes.c_int32)
+    sig = {
+        "pa_status_string": (ctypes.c_char_p, [i32]),
+        "pa_version": (i32, []),
+        "pa_device_error": (i32, [P, I32P]),
+        "pa_deform_balls": (i32, [C, P, i32, P, P]),
+        "pa_forward_workspace_size": (sz, [G, B, i32]),
+        "pa_forward_workspace_size_ex": (sz, [G, B, i32, I32P]),
+        "pa_forward": (i32, [G, B, i32, P, u32, P, sz, P]),
+        "pa_forward_ex": (i32, [G, B, i32, P, u32, I32P, P, sz, P]),
+        "pa_forward_plan_info": (i32, [G, B, i32, I32P, I32P]),
+        "pa_adjoint": (i32, [G, B, C, P, i32, P, P, GR, u32, P]),
+        "pa_loss_workspace_size": (sz, [i64, i32]),
+        "pa_residual_loss": (i32, [P, P, i64, i32, P, P, P, P, sz, P]),
+        "pa_sumsq": (i32, [P, i64, P, P, sz, P]),
+        "pa_count_contributions": (i32, [G, B, i32, P, P]),
+        "pa_adam_step": (i32, [P, P, P, P, i64, ctypes.c_double, ctypes.c_double, ctypes.c_double, ctypes.c_double, i32, P]),
+    }
+    for name, (res, args) in sig.items():
+        fn = getattr(lib, name)
+        fn.restype = res
+        fn.argtypes = args
+    _lib = lib
+    return lib
+
+
+def status_string(status: int) -> str:
+    try:
+        return load().pa_status_string(int(status)).decode()
+    except Exception:  # pragma: no cover
+        return f"status {status}"
+
+
+def check(status: int, where: str) -> None:
+    if status != PA_OK:
+        raise PAError(status, where)
+
+
+def exported_symbols() -> list[str]:
+    """Names of the C-ABI entry points declared in this module."""
+    return ["pa_status_string", "pa_version", "pa_device_error", "pa_deform_balls", "pa_forward_workspace_size",
+            "pa_forward_workspace_size_ex", "pa_forward", "pa_forward_ex", "pa_forward_plan_info", "pa_adjoint",
+            "pa_loss_workspace_size", "pa_residual_loss", "pa_sumsq", "pa_count_contributions", "pa_adam_step"]

@@ -1,0 +1,269 @@
+// Adjoint of the forward projection: gradients of the L2 loss (Sec. 2.2,
+// last paragraph) with respect to the per-frame ball states and, in 4D mode,
+// through Eq. 1-2 to the canonical cloud and the deformation parameters
+// (Sec. 2.2: baseline attributes and (theta, sigma, omega) are learnable).
+//
+// Design (GB300, sm_103a): ball-major, no atomics.
+//  - One warp owns one ball (static mode: one (frame, ball) item) and loops
+//    over all sensors.  The 32 lanes compute the window, phase and gradient
+//    factors of 32 (ball, sensor) pairs in parallel and publish them in
+//    shared memory; the warp then walks each pair's window with lanes on
+//    consecutive samples, reading the residual g[f][s][k] (coalesced, L2
+//    resident) and accumulating per lane
+//        S1 = sum g E u,  S3 = sum g E u (-u^2),  SR = sum g E (1 - tau^2/a^2)
+//    which the per-pair factors fold into per-lane gradient accumulators.
+//  - A warp-shuffle reduction over lanes (i.e. over sensors and samples) at
+//    the end of the ball gives dL/d(x, y, z, a, p); one lane writes it.
+//  - 4D mode recomputes the deformed state of the ball per frame in registers
+//    (never stored) and applies the chain rule of Eq. 1-2, accumulating the
+//    (omega, theta, sigma) gradients in per-warp shared memory across frames.
+//
+// Derivatives used, for v = A tau E, A = p/(2R), E = exp(-tau^2/(2a^2)),
+// tau = R - c t_k, u = tau s, s = K_S/a (so E = 2^(-u^2)):
+//   dv/dp = tau E/(2R)                     -> gp += S1 * a/(2 R K_S)
+//   dv/da = A tau^3 E / a^3                -> ga += S3 * (-A/K_S^3)
+//   dv/dR = -A tau E/R + A E (1 - tau^2/a^2) -> dR = S1 * (-A a/(R K_S)) + A SR
+//   dR/dmu = (mu - x_s)/R.
+#include <algorithm>
+
+#include "pa_internal.h"
+
+namespace pa {
+
+namespace {
+
+constexpr int kAdjWarps = 8;
+
+// dL/d(x, y, z, a, p) of one ball at frame f, summed over all sensors and
+// samples.  Returns the totals (identical in every lane).
+__device__ __forceinline__ void ball_frame_grad(const AdjArgs &A, const float *ssens, float4 *rec, int lane,
+                                                int f, float bx, float by, float bz, float a, float p,
+                                                float out[5], bool &dom) {
+  const int S = A.q.S, T = A.q.T;
+  float gx = 0.f, gy = 0.f, gz = 0.f, ga = 0.f, gp = 0.f;
+  const float *gframe = A.g + (long long)f * S * T;
+  if (a > 0.f && p != 0.f) {
+    for (int s0 = 0; s0 < S; s0 += 32) {
+      const int s = s0 + lane;
+      int W = 0;
+      if (s < S) {
+        const float sx = ssens[s], sy = ssens[S + s], sz = ssens[2 * S + s];
+        const PairWin w = pair_window<false>(A.q, bx, by, bz, a, p, sx, sy, sz, 0, T - 1);
+        dom |= w.domain_err;
+        W = w.W;
+        if (W > 0) {
+          const float invR = __fdividef(1.f, w.R);
+          const float amp = 0.5f * p * invR;        // A = p/(2R)
+          const float aK = a * (1.f / K_S);         // 1/s
+          rec[3 * lane + 0] = make_float4(w.u0, w.du, 0.5f * invR * aK, -amp * (1.f / (K_S * K_S * K_S)));
+          rec[3 * lane + 1] = make_float4(-amp * invR * aK, amp, (bx - sx) * invR, (by - sy) * invR);
+          rec[3 * lane + 2] = make_float4((bz - sz) * invR, __int_as_float(w.klo), __int_as_float(W),
+                                          __int_as_float(s));
+        }
+      }
+      unsigned mask = __ballot_sync(FULL, W > 0);
+      __syncwarp();
+      while (mask) {
+        const int i = __ffs(mask) - 1;
+        mask &= mask - 1;
+        const float4 r0 = rec[3 * i + 0], r1 = rec[3 * i + 1], r2 = rec[3 * i + 2];
+        const int klo = __float_as_int(r2.y), Wi = __float_as_int(r2.z), si = __float_as_int(r2.w);
+        const float *g = gframe + (long long)si * T + klo;
+        float u = fmaf((float)lane, -r0.y, r0.x);
+        const float du32 = 32.f * r0.y;
+        float S1 = 0.f, S3 = 0.f, SR = 0.f;
+        for (int j = lane; j < Wi; j += 32) {
+          const float G = __ldg(g + j);
+          const float arg = -u * u;
+          const float E = ex2(arg);
+          const float ge = G * E;
+          const float gu = ge * u;
+          S1 += gu;
+          S3 = fmaf(gu, arg, S3);
+          SR = fmaf(ge, fmaf(arg, K_2LN2, 1.f), SR);
+          u -= du32;
+        }
+        gp = fmaf(S1, r0.z, gp);
+        ga = fmaf(S3, r0.w, ga);
+        const float dR = fmaf(S1, r1.x, r1.y * SR);
+        gx = fmaf(dR, r1.z, gx);
+        gy = fmaf(dR, r1.w, gy);
+        gz = fmaf(dR, r2.x, gz);
+      }
+      __syncwarp();
+    }
+  }
+  out[0] = warp_sum(gx);
+  out[1] = warp_sum(gy);
+  out[2] = warp_sum(gz);
+  out[3] = warp_sum(ga);
+  out[4] = warp_sum(gp);
+}
+
+__device__ __forceinline__ void load_sensors(const AdjArgs &A, float *ssens) {
+  const int S = A.q.S;
+  for (int i = threadIdx.x; i < 3 * S; i += blockDim.x) {
+    const int c = i / S, s = i - c * S;
+    ssens[i] = A.q.sensors[c * A.q.sstride + s];
+  }
+}
+
+// Static mode: item = (frame, ball).
+__global__ void __launch_bounds__(32 * kAdjWarps) k_adjoint_static(const AdjArgs A) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  float4 *recs = reinterpret_cast<float4 *>(smem_raw);
+  float *ssens = reinterpret_cast<float *>(recs + kAdjWarps * 96);
+  load_sensors(A, ssens);
+  __syncthreads();
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  float4 *rec = recs + warp * 96;
+  bool dom = false;
+  for (long long item = (long long)blockIdx.x * kAdjWarps + warp; item < A.n_items;
+       item += (long long)gridDim.x * kAdjWarps) {
+    const int f = (int)(item / A.n);
+    const long long b = item - (long long)f * A.n;
+    const float *st = A.state + (long long)f * 5 * A.stride;
+    float v[5];
+    // lanes 0..4 fetch the five channels, then broadcast
+    const float mine = lane < 5 ? st[lane * A.stride + b] : 0.f;
+#pragma unroll
+    for (int c = 0; c < 5; ++c) v[c] = __shfl_sync(FULL, mine, c);
+    float g[5];
+    ball_frame_grad(A, ssens, rec, lane, f, v[0], v[1], v[2], v[3], v[4], g, dom);
+    const float sc = A.frame_scale ? __ldg(A.frame_scale + f) : 1.f;
+    if (lane < 5) {
+      float gv = g[0];
+#pragma unroll
+      for (int c = 1; c < 5; ++c)
+        if (lane == c) gv = g[c];
+      gv *= sc;
+      float *dst = A.g_state + (long long)f * 5 * A.stride + lane * A.stride + b;
+      *dst = (A.flags & PA_ACCUMULATE) ? *dst + gv : gv;
+    }
+  }
+  if (dom) set_error(A.err, PA_ERR_DOMAIN);
+}
+
+// 4D mode: item = ball; frames looped inside.
+__global__ void __launch_bounds__(32 * kAdjWarps) k_adjoint_4d(const AdjArgs A) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  const int nb = A.nb;
+  const int per = 5 * nb;
+  float4 *recs = reinterpret_cast<float4 *>(smem_raw);
+  float *ssens = reinterpret_cast<float *>(recs + kAdjWarps * 96);
+  float *wbase = ssens + 3 * A.q.S;  // per warp: om, th, isg, gom, gth, gsg  (6 * per floats)
+  load_sensors(A, ssens);
+  __syncthreads();
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  float4 *rec = recs + warp * 96;
+  float *om = wbase + (size_t)warp * 6 * per;
+  float *th = om + per, *isg = th + per, *gom = isg + per, *gth = gom + per, *gsg = gth + per;
+  const float L2E_HALF = 0.72134752044448170368f;  // log2(e)/2
+  bool dom = false;
+  for (long long b = (long long)blockIdx.x * kAdjWarps + warp; b < A.n_items;
+       b += (long long)gridDim.x * kAdjWarps) {
+    const float mine = lane < 5 ? A.canon[lane * A.stride + b] : 0.f;
+    float q0[5];
+#pragma unroll
+    for (int c = 0; c < 5; ++c) q0[c] = __shfl_sync(FULL, mine, c);
+    for (int i = lane; i < per; i += 32) {
+      const long long gi = (long long)i * A.stride + b;  // [ch][n] rows are contiguous in i
+      om[i] = A.omega[gi];
+      th[i] = A.theta[gi];
+      const float sg = A.sigma[gi];
+      if (!(sg > 0.f)) dom = true;
+      isg[i] = sg > 0.f ? 1.f / sg : 0.f;
+      gom[i] = 0.f;
+      gth[i] = 0.f;
+      gsg[i] = 0.f;
+    }
+    __syncwarp();
+    float gcan[5] = {0.f, 0.f, 0.f, 0.f, 0.f};
+    for (int f = 0; f < A.F; ++f) {
+      const float t = __ldg(A.t_frames + f);
+      float H[5];
+#pragma unroll
+      for (int c = 0; c < 5; ++c) {
+        float h = 0.f;
+        for (int n = lane; n < nb; n += 32) {
+          const int i = c * nb + n;
+          const float d = (t - th[i]) * isg[i];
+          h = fmaf(om[i], ex2(-d * d * L2E_HALF), h);
+        }
+        H[c] = warp_sum(h);
+      }
+      float g[5];
+      ball_frame_grad(A, ssens, rec, lane, f, q0[0] * (1.f + H[0]), q0[1] * (1.f + H[1]), q0[2] * (1.f + H[2]),
+                      q0[3] * (1.f + H[3]), q0[4] * (1.f + H[4]), g, dom);
+      const float sc = A.frame_scale ? __ldg(A.frame_scale + f) : 1.f;
+#pragma unroll
+      for (int c = 0; c < 5; ++c) {
+        const float gc = g[c] * sc;
+        gcan[c] = fmaf(gc, 1.f + H[c], gcan[c]);
+        const float gq = gc * q0[c];
+        for (int n = lane; n < nb; n += 32) {
+          const int i = c * nb + n;
+          const float is = isg[i];
+          const float d = (t - th[i]) * is;          // (t - theta)/sigma
+          const float bn = ex2(-d * d * L2E_HALF);   // basis value
+          const float w = gq * bn;
+          gom[i] += w;
+          const float wo = w * om[i];
+          gth[i] = fmaf(wo, d * is, gth[i]);         // (t - theta)/sigma^2
+          gsg[i] = fmaf(wo, d * d * is, gsg[i]);     // (t - theta)^2/sigma^3
+        }
+      }
+    }
+    __syncwarp();
+    const bool acc = (A.flags & PA_ACCUMULATE) != 0;
+    if (lane < 5) {
+      float gv = gcan[0];
+#pragma unroll
+      for (int c = 1; c < 5; ++c)
+        if (lane == c) gv = gcan[c];
+      float *dst = A.g_state + lane * A.stride + b;
+      *dst = acc ? *dst + gv : gv;
+    }
+    for (int i = lane; i < per; i += 32) {
+      const long long gi = (long long)i * A.stride + b;
+      A.g_omega[gi] = acc ? A.g_omega[gi] + gom[i] : gom[i];
+      A.g_theta[gi] = acc ? A.g_theta[gi] + gth[i] : gth[i];
+      A.g_sigma[gi] = acc ? A.g_sigma[gi] + gsg[i] : gsg[i];
+    }
+    __syncwarp();
+  }
+  if (dom) set_error(A.err, PA_ERR_DOMAIN);
+}
+
+size_t adj_static_smem(int S) { return sizeof(float4) * kAdjWarps * 96 + sizeof(float) * 3 * (size_t)S; }
+size_t adj_4d_smem(int S, int nb) {
+  return adj_static_smem(S) + sizeof(float) * (size_t)kAdjWarps * 6 * 5 * nb;
+}
+
+template <typename K>
+cudaError_t launch_gridstride(K kern, const AdjArgs &a, size_t smem, int sms, cudaStream_t st) {
+  cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  if (e != cudaSuccess) return e;
+  int occ = 0;
+  e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, kern, 32 * kAdjWarps, smem);
+  if (e != cudaSuccess) return e;
+  if (occ < 1) return cudaErrorInvalidConfiguration;
+  const long long need = (a.n_items + kAdjWarps - 1) / kAdjWarps;
+  const long long grid = std::max(1LL, std::min(need, (long long)sms * occ * 4));
+  kern<<<(unsigned)grid, 32 * kAdjWarps, smem, st>>>(a);
+  return cudaGetLastError();
+}
+
+}  // namespace
+
+cudaError_t launch_adjoint_static(const AdjArgs &a, int sms, cudaStream_t st) {
+  if (a.n_items == 0) return cudaSuccess;
+  return launch_gridstride(k_adjoint_static, a, adj_static_smem(a.q.S), sms, st);
+}
+
+cudaError_t launch_adjoint_4d(const AdjArgs &a, int sms, cudaStream_t st) {
+  if (a.n_items == 0) return cudaSuccess;
+  return launch_gridstride(k_adjoint_4d, a, adj_4d_smem(a.q.S, a.nb), sms, st);
+}
+
+}  // namespace pa

@@ -1,0 +1,344 @@
+// C ABI of the library (declared in include/pa.h): host-side validation,
+// tile plans, the per-device error word, and kernel launches.
+#include <cmath>
+#include <cstdint>
+#include <cstring>
+#include <mutex>
+
+#include "pa_internal.h"
+
+namespace {
+
+// One error word per device: kernels record the first data-dependent error.
+__device__ unsigned g_pa_error_word;
+
+constexpr int kMaxDevices = 64;
+
+struct DevInfo {
+  unsigned *err = nullptr;
+  int sms = 0;
+  int max_smem = 0;
+  bool ready = false;
+};
+DevInfo g_dev[kMaxDevices];
+std::mutex g_dev_mu;
+
+const DevInfo *dev_info() {
+  int dev = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= kMaxDevices) return nullptr;
+  std::lock_guard<std::mutex> lk(g_dev_mu);
+  DevInfo &d = g_dev[dev];
+  if (!d.ready) {
+    void *p = nullptr;
+    if (cudaGetSymbolAddress(&p, g_pa_error_word) != cudaSuccess) return nullptr;
+    d.err = static_cast<unsigned *>(p);
+    if (cudaDeviceGetAttribute(&d.sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess) return nullptr;
+    if (cudaDeviceGetAttribute(&d.max_smem, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev) != cudaSuccess)
+      return nullptr;
+    d.ready = true;
+  }
+  return &d;
+}
+
+inline bool aligned(const void *p, uintptr_t a) { return (reinterpret_cast<uintptr_t>(p) & (a - 1)) == 0; }
+inline bool finite_pos(float v) { return std::isfinite(v) && v > 0.f; }
+
+int check_geom(const pa_geom *g) {
+  if (g == nullptr || g->sensors == nullptr) return PA_ERR_INVALID_ARG;
+  if (g->n_sensors < 1 || g->sensor_stride < g->n_sensors) return PA_ERR_INVALID_ARG;
+  if (!finite_pos(g->c) || !finite_pos(g->fs)) return PA_ERR_INVALID_ARG;
+  if (!std::isfinite(g->t0) || g->t0 < 0.f) return PA_ERR_INVALID_ARG;
+  if (g->n_samples < 4 || (g->n_samples & 3) != 0) return PA_ERR_INVALID_ARG;
+  if (!(g->kappa >= 1.f && g->kappa <= 8.f)) return PA_ERR_INVALID_ARG;
+  return PA_OK;
+}
+
+int check_balls(const pa_balls *b) {
+  if (b == nullptr || b->n < 0 || b->stride < b->n || (b->stride & 3) != 0) return PA_ERR_INVALID_ARG;
+  if (b->n > 0 && (b->state == nullptr || !aligned(b->state, 16))) return PA_ERR_INVALID_ARG;
+  return PA_OK;
+}
+
+int check_canon(const pa_canon *c) {
+  if (c == nullptr || c->n < 0 || c->stride < c->n || (c->stride & 3) != 0) return PA_ERR_INVALID_ARG;
+  if (c->n_basis < 1 || c->n_basis > 128) return PA_ERR_INVALID_ARG;
+  if (c->n > 0 && (!c->canon || !c->omega || !c->theta || !c->sigma)) return PA_ERR_INVALID_ARG;
+  return PA_OK;
+}
+
+pa::Acq make_acq(const pa_geom *g) {
+  pa::Acq q;
+  q.sensors = g->sensors;
+  q.S = g->n_sensors;
+  q.sstride = g->sensor_stride;
+  q.T = g->n_samples;
+  q.kappa = g->kappa;
+  const double delta = (double)g->c / (double)g->fs;
+  q.dh = (float)delta;
+  q.dl = (float)(delta - (double)q.dh);
+  const double ct0 = (double)g->c * (double)g->t0;
+  q.ct0h = (float)ct0;
+  q.ct0l = (float)(ct0 - (double)q.ct0h);
+  q.inv_delta = (float)((double)g->fs / (double)g->c);
+  return q;
+}
+
+inline int cuda_status(cudaError_t e) { return e == cudaSuccess ? PA_OK : PA_ERR_CUDA; }
+
+int forward_impl(const pa_geom *geom, const pa_balls *balls, int32_t F, float *traces, uint32_t flags,
+                 const int32_t *tiles, void *ws, size_t ws_bytes, void *stream) {
+  int rc = check_geom(geom);
+  if (rc) return rc;
+  if ((rc = check_balls(balls))) return rc;
+  if (F < 0 || (flags & ~(PA_ACCUMULATE | PA_PROFILE_UNIFORM)) != 0) return PA_ERR_INVALID_ARG;
+  if (F == 0) return PA_OK;
+  if (traces == nullptr || !aligned(traces, 16)) return PA_ERR_INVALID_ARG;
+  const DevInfo *d = dev_info();
+  if (!d) return PA_ERR_CUDA;
+  cudaStream_t st = static_cast<cudaStream_t>(stream);
+  if (balls->n == 0) {
+    if (flags & PA_ACCUMULATE) return PA_OK;
+    return cuda_status(
+        cudaMemsetAsync(traces, 0, sizeof(float) * (size_t)F * geom->n_sensors * geom->n_samples, st));
+  }
+  if (tiles && (tiles[0] < 0 || tiles[0] > 32 || tiles[1] < 0 || tiles[2] < 0 || tiles[3] < 0 ||
+                (tiles[2] & 3) != 0 || (tiles[1] & 3) != 0))
+    return PA_ERR_INVALID_ARG;
+  const pa::FwdPlan p = pa::forward_plan(geom->n_sensors, geom->n_samples, balls->n, F, d->sms,
+                                         tiles ? tiles[0] : 0, tiles ? tiles[1] : 0, tiles ? tiles[2] : 0,
+                                         tiles ? tiles[3] : 0);
+  if ((int)p.smem > d->max_smem) return PA_ERR_INVALID_ARG;
+  if (p.ws_bytes > 0 && (ws == nullptr || ws_bytes < p.ws_bytes || !aligned(ws, 256))) return PA_ERR_WORKSPACE;
+  pa::FwdArgs a;
+  a.q = make_acq(geom);
+  a.state = balls->state;
+  a.n = balls->n;
+  a.stride = balls->stride;
+  a.F = F;
+  a.out = traces;
+  a.partial = static_cast<float *>(ws);
+  a.s_tile = p.s_tile;
+  a.t_tile = p.t_tile;
+  a.nb_tile = p.nb_tile;
+  a.n_splits = p.n_splits;
+  a.n_stiles = p.n_stiles;
+  a.n_ttiles = p.n_ttiles;
+  a.balls_per_split = p.balls_per_split;
+  a.flags = flags;
+  a.err = d->err;
+  return cuda_status(pa::launch_forward(a, p, (flags & PA_PROFILE_UNIFORM) != 0, st));
+}
+
+}  // namespace
+
+extern "C" {
+
+const char *pa_status_string(int32_t status) {
+  switch (status) {
+    case PA_OK: return "PA_OK";
+    case PA_ERR_INVALID_ARG: return "PA_ERR_INVALID_ARG: invalid argument";
+    case PA_ERR_DOMAIN: return "PA_ERR_DOMAIN: sensor inside a ball support or non-positive basis width";
+    case PA_ERR_CUDA: return "PA_ERR_CUDA: CUDA runtime error";
+    case PA_ERR_TIMEOUT: return "PA_ERR_TIMEOUT: bounded wait ran out inside a kernel";
+    case PA_ERR_WORKSPACE: return "PA_ERR_WORKSPACE: workspace missing, misaligned or too small";
+    default: return "unknown status";
+  }
+}
+
+int32_t pa_version(void) { return 100; }
+
+int32_t pa_device_error(void *stream, int32_t *out) {
+  if (out == nullptr) return PA_ERR_INVALID_ARG;
+  const DevInfo *d = dev_info();
+  if (!d) return PA_ERR_CUDA;
+  cudaStream_t st = static_cast<cudaStream_t>(stream);
+  unsigned v = 0;
+  cudaError_t e = cudaMemcpyAsync(&v, d->err, sizeof(unsigned), cudaMemcpyDeviceToHost, st);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+  if (e == cudaSuccess) e = cudaMemsetAsync(d->err, 0, sizeof(unsigned), st);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+  if (e != cudaSuccess) return PA_ERR_CUDA;
+  *out = (int32_t)v;
+  return PA_OK;
+}
+
+int32_t pa_deform_balls(const pa_canon *canon, const float *t_frames, int32_t n_frames, float *state_out,
+                        void *stream) {
+  int rc = check_canon(canon);
+  if (rc) return rc;
+  if (n_frames < 0) return PA_ERR_INVALID_ARG;
+  if (n_frames == 0 || canon->n == 0) return PA_OK;
+  if (t_frames == nullptr || state_out == nullptr) return PA_ERR_INVALID_ARG;
+  const DevInfo *d = dev_info();
+  if (!d) return PA_ERR_CUDA;
+  return cuda_status(pa::launch_deform(canon->canon, canon->omega, canon->theta, canon->sigma, canon->n,
+                                       canon->stride, canon->n_basis, t_frames, n_frames, state_out, d->err,
+                                       static_cast<cudaStream_t>(stream)));
+}
+
+size_t pa_forward_workspace_size_ex(const pa_geom *geom, const pa_balls *balls, int32_t n_frames,
+                                    const int32_t *tiles) {
+  if (check_geom(geom) || check_balls(balls) || n_frames <= 0 || balls->n == 0) return 0;
+  const DevInfo *d = dev_info();
+  if (!d) return 0;
+  const pa::FwdPlan p = pa::forward_plan(geom->n_sensors, geom->n_samples, balls->n, n_frames, d->sms,
+                                         tiles ? tiles[0] : 0, tiles ? tiles[1] : 0, tiles ? tiles[2] : 0,
+                                         tiles ? tiles[3] : 0);
+  return p.ws_bytes;
+}
+
+size_t pa_forward_workspace_size(const pa_geom *geom, const pa_balls *balls, int32_t n_frames) {
+  return pa_forward_workspace_size_ex(geom, balls, n_frames, nullptr);
+}
+
+int32_t pa_forward(const pa_geom *geom, const pa_balls *balls, int32_t n_frames, float *traces, uint32_t flags,
+                   void *workspace, size_t workspace_bytes, void *stream) {
+  return forward_impl(geom, balls, n_frames, traces, flags, nullptr, workspace, workspace_bytes, stream);
+}
+
+int32_t pa_forward_ex(const pa_geom *geom, const pa_balls *balls, int32_t n_frames, float *traces, uint32_t flags,
+                      const int32_t *tiles, void *workspace, size_t workspace_bytes, void *stream) {
+  return forward_impl(geom, balls, n_frames, traces, flags, tiles, workspace, workspace_bytes, stream);
+}
+
+int32_t pa_forward_plan_info(const pa_geom *geom, const pa_balls *balls, int32_t n_frames, const int32_t *tiles,
+                             int32_t *out6) {
+  if (out6 == nullptr) return PA_ERR_INVALID_ARG;
+  int rc = check_geom(geom);
+  if (rc) return rc;
+  if ((rc = check_balls(balls))) return rc;
+  if (n_frames <= 0) return PA_ERR_INVALID_ARG;
+  const DevInfo *d = dev_info();
+  if (!d) return PA_ERR_CUDA;
+  const pa::FwdPlan p = pa::forward_plan(geom->n_sensors, geom->n_samples, balls->n, n_frames, d->sms,
+                                         tiles ? tiles[0] : 0, tiles ? tiles[1] : 0, tiles ? tiles[2] : 0,
+                                         tiles ? tiles[3] : 0);
+  out6[0] = p.s_tile;
+  out6[1] = p.t_tile;
+  out6[2] = p.nb_tile;
+  out6[3] = p.n_splits;
+  out6[4] = (int32_t)((long long)n_frames * p.n_stiles * p.n_ttiles * p.n_splits);
+  out6[5] = (int32_t)p.smem;
+  return PA_OK;
+}
+
+int32_t pa_adjoint(const pa_geom *geom, const pa_balls *balls, const pa_canon *canon, const float *t_frames,
+                   int32_t n_frames, const float *trace_grad, const float *frame_scale, pa_grads *grads,
+                   uint32_t flags, void *stream) {
+  int rc = check_geom(geom);
+  if (rc) return rc;
+  if (n_frames < 0 || grads == nullptr || (flags & ~PA_ACCUMULATE) != 0) return PA_ERR_INVALID_ARG;
+  const bool four_d = canon != nullptr;
+  if ((balls != nullptr) == four_d) return PA_ERR_INVALID_ARG;  // exactly one mode
+  if (four_d) {
+    if ((rc = check_canon(canon))) return rc;
+    if (canon->n > 0 && (!grads->state || !grads->omega || !grads->theta || !grads->sigma))
+      return PA_ERR_INVALID_ARG;
+    if (n_frames > 0 && t_frames == nullptr) return PA_ERR_INVALID_ARG;
+  } else {
+    if ((rc = check_balls(balls))) return rc;
+    if (balls->n > 0 && grads->state == nullptr) return PA_ERR_INVALID_ARG;
+  }
+  const long long n = four_d ? canon->n : balls->n;
+  if (n == 0) return PA_OK;
+  if (n_frames > 0 && trace_grad == nullptr) return PA_ERR_INVALID_ARG;
+  const DevInfo *d = dev_info();
+  if (!d) return PA_ERR_CUDA;
+  cudaStream_t st = static_cast<cudaStream_t>(stream);
+  pa::AdjArgs a;
+  std::memset(&a, 0, sizeof(a));
+  a.q = make_acq(geom);
+  a.F = n_frames;
+  a.g = trace_grad;
+  a.frame_scale = frame_scale;
+  a.g_state = grads->state;
+  a.flags = flags;
+  a.err = d->err;
+  a.n = n;
+  if (four_d) {
+    a.canon = canon->canon;
+    a.omega = canon->omega;
+    a.theta = canon->theta;
+    a.sigma = canon->sigma;
+    a.nb = canon->n_basis;
+    a.stride = canon->stride;
+    a.t_frames = t_frames;
+    a.g_omega = grads->omega;
+    a.g_theta = grads->theta;
+    a.g_sigma = grads->sigma;
+    a.n_items = n;
+    const size_t smem = sizeof(float4) * 8 * 96 + sizeof(float) * 3 * (size_t)geom->n_sensors +
+                        sizeof(float) * 8 * 6 * 5 * (size_t)canon->n_basis;
+    if ((long long)smem > d->max_smem) return PA_ERR_INVALID_ARG;
+    if (n_frames == 0) {
+      // no frame contributes: gradients are zero
+      if (flags & PA_ACCUMULATE) return PA_OK;
+      const size_t rows = sizeof(float) * (size_t)canon->stride;
+      cudaError_t e = cudaMemsetAsync(grads->state, 0, rows * 5, st);
+      if (e == cudaSuccess) e = cudaMemsetAsync(grads->omega, 0, rows * 5 * canon->n_basis, st);
+      if (e == cudaSuccess) e = cudaMemsetAsync(grads->theta, 0, rows * 5 * canon->n_basis, st);
+      if (e == cudaSuccess) e = cudaMemsetAsync(grads->sigma, 0, rows * 5 * canon->n_basis, st);
+      return cuda_status(e);
+    }
+    return cuda_status(pa::launch_adjoint_4d(a, d->sms, st));
+  }
+  a.state = balls->state;
+  a.stride = balls->stride;
+  a.n_items = (long long)n_frames * n;
+  const size_t smem = sizeof(float4) * 8 * 96 + sizeof(float) * 3 * (size_t)geom->n_sensors;
+  if ((long long)smem > d->max_smem) return PA_ERR_INVALID_ARG;
+  return cuda_status(pa::launch_adjoint_static(a, d->sms, st));
+}
+
+size_t pa_loss_workspace_size(int64_t per_frame, int32_t n_frames) {
+  if (per_frame <= 0 || n_frames <= 0) return 0;
+  return sizeof(double) * (size_t)n_frames * pa::loss_blocks_per_frame(per_frame);
+}
+
+int32_t pa_residual_loss(const float *pred, const float *meas, int64_t per_frame, int32_t n_frames,
+                         const float *frame_scale, double *loss, float *resid, void *workspace,
+                         size_t workspace_bytes, void *stream) {
+  if (per_frame < 4 || (per_frame & 3) != 0 || n_frames < 0) return PA_ERR_INVALID_ARG;
+  if (n_frames == 0) return PA_OK;
+  if (!pred || !meas || !aligned(pred, 16) || !aligned(meas, 16)) return PA_ERR_INVALID_ARG;
+  if (resid && !aligned(resid, 16)) return PA_ERR_INVALID_ARG;
+  if (!loss && !resid) return PA_ERR_INVALID_ARG;
+  const size_t need = pa_loss_workspace_size(per_frame, n_frames);
+  if (workspace == nullptr || workspace_bytes < need || !aligned(workspace, 16)) return PA_ERR_WORKSPACE;
+  return cuda_status(pa::launch_loss(pred, meas, per_frame, n_frames, frame_scale, loss, resid,
+                                     static_cast<double *>(workspace), pa::loss_blocks_per_frame(per_frame),
+                                     static_cast<cudaStream_t>(stream)));
+}
+
+int32_t pa_sumsq(const float *x, int64_t n, double *out, void *workspace, size_t workspace_bytes, void *stream) {
+  if (n < 4 || (n & 3) != 0 || !x || !out || !aligned(x, 16)) return PA_ERR_INVALID_ARG;
+  const size_t need = pa_loss_workspace_size(n, 1);
+  if (workspace == nullptr || workspace_bytes < need || !aligned(workspace, 16)) return PA_ERR_WORKSPACE;
+  return cuda_status(pa::launch_loss(x, nullptr, n, 1, nullptr, out, nullptr, static_cast<double *>(workspace),
+                                     pa::loss_blocks_per_frame(n), static_cast<cudaStream_t>(stream)));
+}
+
+int32_t pa_count_contributions(const pa_geom *geom, const pa_balls *balls, int32_t n_frames,
+                               unsigned long long *out, void *stream) {
+  int rc = check_geom(geom);
+  if (rc) return rc;
+  if ((rc = check_balls(balls))) return rc;
+  if (n_frames < 0 || out == nullptr) return PA_ERR_INVALID_ARG;
+  return cuda_status(pa::launch_count(make_acq(geom), balls->state, balls->n, balls->stride, n_frames, out,
+                                      static_cast<cudaStream_t>(stream)));
+}
+
+int32_t pa_adam_step(float *x, const float *g, float *m, float *v, int64_t n, double lr, double beta1, double beta2,
+                     double eps, int32_t step, void *stream) {
+  if (n < 0 || step < 1 || !(beta1 >= 0.0 && beta1 < 1.0) || !(beta2 >= 0.0 && beta2 < 1.0) || !(eps > 0.0))
+    return PA_ERR_INVALID_ARG;
+  if (n == 0) return PA_OK;
+  if (!x || !g || !m || !v || !aligned(x, 16) || !aligned(g, 16) || !aligned(m, 16) || !aligned(v, 16))
+    return PA_ERR_INVALID_ARG;
+  const float bc1 = (float)(1.0 - std::pow(beta1, (double)step));
+  const float bc2 = (float)(1.0 - std::pow(beta2, (double)step));
+  return cuda_status(pa::launch_adam(x, g, m, v, n, (float)lr, (float)beta1, (float)beta2, (float)(1.0 - beta1),
+                                     (float)(1.0 - beta2), (float)eps, bc1, bc2, static_cast<cudaStream_t>(stream)));
+}
+
+}  // extern "C"

@@ -1,0 +1,292 @@
+// Forward projection kernel (the radiator of Sec. 2.2, last paragraph) and
+// the contribution counter.
+//
+// Design (GB300, sm_103a):
+//  - One CTA owns a tile of s_tile sensors x t_tile samples of one frame and a
+//    range of balls.  Each warp owns one sensor: its trace tile lives in
+//    shared memory and only that warp writes it, so accumulation is a plain
+//    load-add-store with no atomics.
+//  - Ball tiles (x, y, z, a, p rows of nb_tile balls) are streamed from HBM
+//    into shared memory by TMA bulk copies (cp.async.bulk) completing on
+//    mbarriers, double buffered, issued by one thread.
+//  - Per 32-ball chunk, the 32 lanes compute the window and phase of 32
+//    (ball, sensor) pairs in parallel (double-float distance, once per pair),
+//    publish them in shared memory, and then the warp walks each pair's
+//    arrival window with lanes on consecutive samples (conflict-free shared
+//    accesses): u -= 32 du; v = amp * u * 2^(-u^2); trace[k] += v.
+//  - Trace tiles are flushed with coalesced float4 stores.  With more than
+//    one ball split, partial traces go to the workspace and a second kernel
+//    sums them in split order (deterministic).
+#include <algorithm>
+
+#include "pa_internal.h"
+
+namespace pa {
+
+namespace {
+
+constexpr int kMaxThreads = 1024;
+
+template <bool UNIFORM>
+__global__ void __launch_bounds__(kMaxThreads) k_forward(const FwdArgs A) {
+  extern __shared__ __align__(128) unsigned char smem_raw[];
+  uint64_t *bars = reinterpret_cast<uint64_t *>(smem_raw);
+  float *sball = reinterpret_cast<float *>(smem_raw + 128);
+  float4 *srec = reinterpret_cast<float4 *>(sball + 2 * 5 * A.nb_tile);
+  float *str = reinterpret_cast<float *>(srec + A.s_tile * 32);
+
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  int item = blockIdx.x;
+  const int split = item % A.n_splits;
+  item /= A.n_splits;
+  const int tt = item % A.n_ttiles;
+  item /= A.n_ttiles;
+  const int st = item % A.n_stiles;
+  const int f = item / A.n_stiles;
+
+  const int T = A.q.T;
+  const int k0 = tt * A.t_tile;
+  const int klen = min(A.t_tile, T - k0);
+  const int s = st * A.s_tile + warp;
+  const bool s_ok = s < A.q.S;
+  const long long b_begin = (long long)split * A.balls_per_split;
+  const long long b_end = min(A.n, b_begin + A.balls_per_split);
+  const int ntiles = b_end > b_begin ? (int)((b_end - b_begin + A.nb_tile - 1) / A.nb_tile) : 0;
+  const float *state_f = A.state + (long long)f * 5 * A.stride;
+  const int nbt = A.nb_tile;
+
+  float4 *str4 = reinterpret_cast<float4 *>(str);
+  const int nz = A.s_tile * A.t_tile / 4;
+  for (int i = tid; i < nz; i += blockDim.x) str4[i] = make_float4(0.f, 0.f, 0.f, 0.f);
+  if (tid == 0) {
+    mbar_init(&bars[0], 1);
+    mbar_init(&bars[1], 1);
+    fence_barrier_init();
+  }
+  __syncthreads();
+
+  auto issue = [&](int t) {
+    const int stage = t & 1;
+    const long long b0 = b_begin + (long long)t * nbt;
+    const int cnt = (int)min((long long)nbt, b_end - b0);
+    const unsigned bytes = (unsigned)(((cnt + 3) & ~3) * 4);
+    mbar_arrive_expect_tx(&bars[stage], 5u * bytes);
+#pragma unroll
+    for (int ch = 0; ch < 5; ++ch)
+      bulk_copy_g2s(sball + (stage * 5 + ch) * nbt, state_f + ch * A.stride + b0, bytes, &bars[stage]);
+  };
+  if (tid == 0) {
+    fence_proxy_async();
+    if (ntiles > 0) issue(0);
+    if (ntiles > 1) issue(1);
+  }
+
+  float sx = 0.f, sy = 0.f, sz = 0.f;
+  if (s_ok) {
+    sx = A.q.sensors[s];
+    sy = A.q.sensors[A.q.sstride + s];
+    sz = A.q.sensors[2 * A.q.sstride + s];
+  }
+  float *mytr = str + warp * A.t_tile;
+  float4 *myrec = srec + warp * 32;
+  bool dom = false;
+
+  for (int t = 0; t < ntiles; ++t) {
+    const int stage = t & 1;
+    const bool ok = mbar_wait_bounded(&bars[stage], (t >> 1) & 1);
+    const int cnt = (int)min((long long)nbt, b_end - (b_begin + (long long)t * nbt));
+    if (ok && s_ok) {
+      const float *bx = sball + stage * 5 * nbt;
+      for (int c0 = 0; c0 < cnt; c0 += 32) {
+        const int bi = c0 + lane;
+        PairWin w;
+        w.W = 0;
+        w.domain_err = false;
+        if (bi < cnt)
+          w = pair_window<UNIFORM>(A.q, bx[bi], bx[nbt + bi], bx[2 * nbt + bi], bx[3 * nbt + bi],
+                                   bx[4 * nbt + bi], sx, sy, sz, k0, k0 + klen - 1);
+        dom |= w.domain_err;
+        if (w.W > 0) myrec[lane] = make_float4(w.u0, w.du, w.amp, __int_as_float((w.klo - k0) | (w.W << 16)));
+        unsigned mask = __ballot_sync(FULL, w.W > 0);
+        __syncwarp();
+        while (mask) {
+          const int i = __ffs(mask) - 1;
+          mask &= mask - 1;
+          const float4 r = myrec[i];
+          const int packed = __float_as_int(r.w);
+          const int kl = packed & 0xffff, W = packed >> 16;
+          float u = fmaf((float)lane, -r.y, r.x);
+          const float du32 = 32.f * r.y;
+          float *tr = mytr + kl;
+          for (int j = lane; j < W; j += 32) {
+            const float E = UNIFORM ? 1.f : ex2(-u * u);
+            tr[j] = fmaf(r.z * u, E, tr[j]);
+            u -= du32;
+          }
+          __syncwarp();
+        }
+      }
+    }
+    const int abort = __syncthreads_or(!ok);
+    if (abort) {
+      // A copy did not complete in time: record it, give the copies still in
+      // flight a bounded chance to land, and leave without writing output.
+      if (tid == 0) {
+        set_error(A.err, PA_ERR_TIMEOUT);
+        mbar_wait_bounded(&bars[t & 1], (t >> 1) & 1);
+        if (t + 1 < ntiles) mbar_wait_bounded(&bars[(t + 1) & 1], ((t + 1) >> 1) & 1);
+      }
+      __syncthreads();
+      return;
+    }
+    if (tid == 0 && t + 2 < ntiles) {
+      fence_proxy_async();
+      issue(t + 2);
+    }
+  }
+  if (dom) set_error(A.err, PA_ERR_DOMAIN);
+
+  if (s_ok) {
+    const long long base = ((long long)f * A.q.S + s) * T + k0;
+    const bool single = A.n_splits == 1;
+    float *dst = single ? A.out + base : A.partial + (long long)split * A.F * A.q.S * T + base;
+    const bool acc = single && (A.flags & PA_ACCUMULATE);
+    float4 *d4 = reinterpret_cast<float4 *>(dst);
+    const float4 *s4 = reinterpret_cast<const float4 *>(mytr);
+    for (int i = lane; i < klen / 4; i += 32) {
+      float4 v = s4[i];
+      if (acc) {
+        const float4 o = d4[i];
+        v.x += o.x;
+        v.y += o.y;
+        v.z += o.z;
+        v.w += o.w;
+      }
+      d4[i] = v;
+    }
+  }
+}
+
+// out[i] (+)= sum over splits of partial[split][i], splits in order.
+__global__ void k_reduce_splits(const float4 *__restrict__ partial, float4 *__restrict__ out,
+                                long long n4, int n_splits, bool accumulate) {
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n4;
+       i += (long long)gridDim.x * blockDim.x) {
+    float4 v = accumulate ? out[i] : make_float4(0.f, 0.f, 0.f, 0.f);
+    for (int sp = 0; sp < n_splits; ++sp) {
+      const float4 p = __ldg(&partial[sp * n4 + i]);
+      v.x += p.x;
+      v.y += p.y;
+      v.z += p.z;
+      v.w += p.w;
+    }
+    out[i] = v;
+  }
+}
+
+__global__ void k_count(const Acq q, const float *state, long long n, long long stride, int F,
+                        unsigned long long *out) {
+  const long long total = (long long)F * q.S * n;
+  unsigned long long mine = 0;
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < total;
+       i += (long long)gridDim.x * blockDim.x) {
+    const long long b = i % n;
+    const long long fs = i / n;
+    const int s = (int)(fs % q.S);
+    const int f = (int)(fs / q.S);
+    const float *st = state + (long long)f * 5 * stride;
+    const PairWin w = pair_window<false>(q, st[b], st[stride + b], st[2 * stride + b], st[3 * stride + b],
+                                         st[4 * stride + b], q.sensors[s], q.sensors[q.sstride + s],
+                                         q.sensors[2 * q.sstride + s], 0, q.T - 1);
+    mine += (unsigned long long)w.W;
+  }
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) mine += __shfl_xor_sync(FULL, mine, o);
+  if ((threadIdx.x & 31) == 0 && mine) atomicAdd(out, mine);
+}
+
+}  // namespace
+
+size_t forward_smem_bytes(int s_tile, int t_tile, int nb_tile) {
+  return 128 + sizeof(float) * (size_t)(2 * 5 * nb_tile) + sizeof(float4) * (size_t)(s_tile * 32) +
+         sizeof(float) * (size_t)s_tile * t_tile;
+}
+
+int forward_blocks_per_sm(const FwdPlan &p, bool uniform) {
+  int nb = 0;
+  auto fn = uniform ? k_forward<true> : k_forward<false>;
+  cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)p.smem);
+  cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, fn, 32 * p.s_tile, p.smem);
+  return nb;
+}
+
+FwdPlan forward_plan(int S, int T, long long n, int F, int sms, int s_tile_o, int t_tile_o,
+                     int nb_tile_o, int splits_o) {
+  FwdPlan p{};
+  p.s_tile = s_tile_o > 0 ? s_tile_o : 8;
+  // Whole trace per CTA when it fits comfortably, else 2048-sample tiles.
+  int tt = t_tile_o > 0 ? t_tile_o : (T <= 4096 ? T : 2048);
+  tt = std::min(std::min(tt, T), 16384);
+  tt = (tt + 3) & ~3;
+  p.t_tile = tt;
+  p.nb_tile = nb_tile_o > 0 ? nb_tile_o : 512;
+  p.n_stiles = (S + p.s_tile - 1) / p.s_tile;
+  p.n_ttiles = (T + p.t_tile - 1) / p.t_tile;
+  p.smem = forward_smem_bytes(p.s_tile, p.t_tile, p.nb_tile);
+  const long long base_ctas = std::max(1LL, (long long)F * p.n_stiles * p.n_ttiles);
+  const long long max_splits = std::max(1LL, (n + p.nb_tile - 1) / p.nb_tile);
+  long long splits = 1;
+  if (splits_o > 0) {
+    splits = splits_o;
+  } else {
+    // Smallest number of ball splits whose CTA count fills whole waves to at
+    // least 90% (the per-CTA work is uniform across tiles).
+    const long long slots = (long long)sms * std::max(1, forward_blocks_per_sm(p, false));
+    for (long long waves = 1; waves <= 16; ++waves) {
+      const long long sp = std::max(1LL, (waves * slots + base_ctas / 2) / base_ctas);
+      const long long ctas = base_ctas * sp;
+      const long long used = (ctas + slots - 1) / slots * slots;
+      splits = sp;
+      if (ctas >= slots && (double)ctas / (double)used >= 0.9) break;
+      if (sp >= max_splits) break;
+    }
+  }
+  splits = std::max(1LL, std::min(splits, max_splits));
+  // balls per split: multiple of 4 so every TMA source stays 16-byte aligned
+  long long bps = (n + splits - 1) / splits;
+  bps = (bps + 3) & ~3LL;
+  if (bps <= 0) bps = 4;
+  p.balls_per_split = bps;
+  p.n_splits = (int)std::max(1LL, (n + bps - 1) / bps);
+  p.ws_bytes = p.n_splits > 1 ? sizeof(float) * (size_t)p.n_splits * F * S * T : 0;
+  return p;
+}
+
+cudaError_t launch_forward(const FwdArgs &a, const FwdPlan &p, bool uniform, cudaStream_t st) {
+  auto fn = uniform ? k_forward<true> : k_forward<false>;
+  cudaError_t e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)p.smem);
+  if (e != cudaSuccess) return e;
+  const long long grid = (long long)a.F * p.n_stiles * p.n_ttiles * p.n_splits;
+  fn<<<(unsigned)grid, 32 * p.s_tile, p.smem, st>>>(a);
+  e = cudaGetLastError();
+  if (e != cudaSuccess || p.n_splits == 1) return e;
+  const long long n4 = (long long)a.F * a.q.S * a.q.T / 4;
+  const long long blocks = std::min<long long>((n4 + 255) / 256, 152LL * 16);
+  k_reduce_splits<<<(unsigned)std::max(1LL, blocks), 256, 0, st>>>(
+      reinterpret_cast<const float4 *>(a.partial), reinterpret_cast<float4 *>(a.out), n4, p.n_splits,
+      (a.flags & PA_ACCUMULATE) != 0);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_count(const Acq &q, const float *state, long long n, long long stride, int F,
+                         unsigned long long *out, cudaStream_t st) {
+  cudaError_t e = cudaMemsetAsync(out, 0, sizeof(unsigned long long), st);
+  if (e != cudaSuccess) return e;
+  const long long total = (long long)F * q.S * n;
+  if (total == 0) return cudaSuccess;
+  const long long blocks = std::min<long long>((total + 255) / 256, 152LL * 32);
+  k_count<<<(unsigned)blocks, 256, 0, st>>>(q, state, n, stride, F, out);
+  return cudaGetLastError();
+}
+
+}  // namespace pa

@@ -1,0 +1,77 @@
+// Internal (host-side) interface between the C-ABI layer (pa_api.cu) and the
+// kernel translation units.  Not part of the public ABI.
+#pragma once
+
+#include <cstddef>
+#include <cstdint>
+
+#include "pa_common.cuh"
+
+namespace pa {
+
+// Tile plan of one pa_forward call.
+struct FwdPlan {
+  int s_tile;      // sensors per CTA (one warp each)
+  int t_tile;      // samples per CTA
+  int nb_tile;     // balls per TMA stage
+  int n_splits;    // ball-range splits (partial traces summed by a second kernel)
+  int n_stiles, n_ttiles;
+  long long balls_per_split;
+  size_t smem;     // dynamic shared memory per CTA
+  size_t ws_bytes; // workspace for split partials
+};
+
+struct FwdArgs {
+  Acq q;
+  const float *state;
+  long long n, stride;
+  int F;
+  float *out;
+  float *partial;
+  int s_tile, t_tile, nb_tile, n_splits, n_stiles, n_ttiles;
+  long long balls_per_split;
+  unsigned flags;
+  unsigned *err;
+};
+
+struct AdjArgs {
+  Acq q;
+  // static mode
+  const float *state;
+  // 4D mode
+  const float *canon, *omega, *theta, *sigma;
+  int nb;
+  const float *t_frames;
+  long long n, stride;
+  int F;
+  const float *g;
+  const float *frame_scale;
+  float *g_state, *g_omega, *g_theta, *g_sigma;
+  unsigned flags;
+  unsigned *err;
+  long long n_items;
+};
+
+// Plan selection (tile sizes, splits); `override` entries > 0 replace the
+// heuristic (used by the autotuner).
+FwdPlan forward_plan(int S, int T, long long n, int F, int sms, int s_tile_override,
+                     int t_tile_override, int nb_tile_override, int splits_override);
+size_t forward_smem_bytes(int s_tile, int t_tile, int nb_tile);
+int forward_blocks_per_sm(const FwdPlan &p, bool uniform);
+
+cudaError_t launch_forward(const FwdArgs &a, const FwdPlan &p, bool uniform, cudaStream_t st);
+cudaError_t launch_count(const Acq &q, const float *state, long long n, long long stride, int F,
+                         unsigned long long *out, cudaStream_t st);
+cudaError_t launch_adjoint_static(const AdjArgs &a, int sms, cudaStream_t st);
+cudaError_t launch_adjoint_4d(const AdjArgs &a, int sms, cudaStream_t st);
+cudaError_t launch_deform(const float *canon, const float *omega, const float *theta,
+                          const float *sigma, long long n, long long stride, int nb,
+                          const float *t, int F, float *out, unsigned *err, cudaStream_t st);
+cudaError_t launch_loss(const float *pred, const float *meas, long long per_frame, int F,
+                        const float *scale, double *loss, float *resid, double *partials,
+                        int blocks_per_frame, cudaStream_t st);
+int loss_blocks_per_frame(long long per_frame);
+cudaError_t launch_adam(float *x, const float *g, float *m, float *v, long long n, float lr, float b1,
+                        float b2, float omb1, float omb2, float eps, float bc1, float bc2, cudaStream_t st);
+
+}  // namespace pa

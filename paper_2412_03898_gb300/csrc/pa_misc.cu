@@ -1,0 +1,182 @@
+// Deformation (Eq. 1-2), the FP64 L2 loss / residual, and Adam.
+#include <algorithm>
+
+#include "pa_internal.h"
+
+namespace pa {
+
+namespace {
+
+constexpr int kFrameChunk = 8;
+
+// Eq. 1-2: one thread per (ball, chunk of up to kFrameChunk frames).  The
+// deformation parameters of a ball are read once per chunk; reads are
+// coalesced across threads (ball index fastest).
+__global__ void __launch_bounds__(256) k_deform(const float *__restrict__ canon, const float *__restrict__ omega,
+                                                const float *__restrict__ theta, const float *__restrict__ sigma,
+                                                long long n, long long stride, int nb,
+                                                const float *__restrict__ t, int F, float *__restrict__ out,
+                                                unsigned *err) {
+  const float L2E_HALF = 0.72134752044448170368f;  // log2(e)/2
+  const int nchunks = (F + kFrameChunk - 1) / kFrameChunk;
+  const long long total = n * nchunks;
+  bool dom = false;
+  for (long long it = blockIdx.x * (long long)blockDim.x + threadIdx.x; it < total;
+       it += (long long)gridDim.x * blockDim.x) {
+    const long long b = it % n;
+    const int f0 = (int)(it / n) * kFrameChunk;
+    const int fc = min(kFrameChunk, F - f0);
+    float tf[kFrameChunk];
+#pragma unroll
+    for (int j = 0; j < kFrameChunk; ++j) tf[j] = j < fc ? __ldg(t + f0 + j) : 0.f;
+    for (int c = 0; c < 5; ++c) {
+      float H[kFrameChunk];
+#pragma unroll
+      for (int j = 0; j < kFrameChunk; ++j) H[j] = 0.f;
+      for (int k = 0; k < nb; ++k) {
+        const long long gi = ((long long)c * nb + k) * stride + b;
+        const float om = __ldg(omega + gi), th = __ldg(theta + gi), sg = __ldg(sigma + gi);
+        if (!(sg > 0.f)) {
+          dom = true;
+          continue;
+        }
+        const float is = 1.f / sg;
+#pragma unroll
+        for (int j = 0; j < kFrameChunk; ++j) {
+          const float d = (tf[j] - th) * is;
+          H[j] = fmaf(om, ex2(-d * d * L2E_HALF), H[j]);
+        }
+      }
+      const float q0 = __ldg(canon + (long long)c * stride + b);
+#pragma unroll
+      for (int j = 0; j < kFrameChunk; ++j)
+        if (j < fc) out[((long long)(f0 + j) * 5 + c) * stride + b] = q0 * (1.f + H[j]);
+    }
+  }
+  if (dom) set_error(err, PA_ERR_DOMAIN);
+}
+
+// Per-frame partial sums of squared residuals in FP64 (each float4 is summed
+// in fp32 then promoted), optional residual 2 scale (pred - meas).
+__global__ void __launch_bounds__(256) k_loss_partial(const float4 *__restrict__ pred, const float4 *__restrict__ meas,
+                                                      long long per4, const float *__restrict__ scale,
+                                                      float4 *__restrict__ resid, double *__restrict__ partials) {
+  const int f = blockIdx.y;
+  const float4 *p = pred + (long long)f * per4;
+  const float4 *m = meas ? meas + (long long)f * per4 : nullptr;
+  float4 *r = resid ? resid + (long long)f * per4 : nullptr;
+  const float two_s = 2.f * (scale ? __ldg(scale + f) : 1.f);
+  double acc = 0.0;
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < per4;
+       i += (long long)gridDim.x * blockDim.x) {
+    float4 d = __ldg(p + i);
+    if (m) {
+      const float4 q = __ldg(m + i);
+      d.x -= q.x;
+      d.y -= q.y;
+      d.z -= q.z;
+      d.w -= q.w;
+    }
+    acc += (double)fmaf(d.x, d.x, fmaf(d.y, d.y, fmaf(d.z, d.z, d.w * d.w)));
+    if (r) r[i] = make_float4(two_s * d.x, two_s * d.y, two_s * d.z, two_s * d.w);
+  }
+  __shared__ double red[8];
+  acc = warp_sum_d(acc);
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  if (lane == 0) red[warp] = acc;
+  __syncthreads();
+  if (warp == 0) {
+    double v = lane < (int)(blockDim.x >> 5) ? red[lane] : 0.0;
+    v = warp_sum_d(v);
+    if (lane == 0) partials[(long long)f * gridDim.x + blockIdx.x] = v;
+  }
+}
+
+// loss[f] = sum of the frame's partials, in a fixed order.
+__global__ void k_loss_final(const double *__restrict__ partials, int bpf, double *__restrict__ loss) {
+  const int f = blockIdx.x, lane = threadIdx.x;
+  double v = 0.0;
+  for (int i = lane; i < bpf; i += 32) v += partials[(long long)f * bpf + i];
+  v = warp_sum_d(v);
+  if (lane == 0) loss[f] = v;
+}
+
+__global__ void k_adam(float4 *__restrict__ x, const float4 *__restrict__ g, float4 *__restrict__ m,
+                       float4 *__restrict__ v, long long n4, float lr, float b1, float b2, float omb1, float omb2,
+                       float eps, float bc1, float bc2) {
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n4;
+       i += (long long)gridDim.x * blockDim.x) {
+    float4 xi = x[i], gi = __ldg(g + i), mi = m[i], vi = v[i];
+    float *px = &xi.x, *pg = &gi.x, *pm = &mi.x, *pv = &vi.x;
+#pragma unroll
+    for (int k = 0; k < 4; ++k) {
+      pm[k] = fmaf(b1, pm[k], omb1 * pg[k]);
+      pv[k] = fmaf(b2, pv[k], omb2 * pg[k] * pg[k]);
+      const float mh = pm[k] / bc1;
+      const float vh = pv[k] / bc2;
+      px[k] -= lr * mh / (sqrtf(vh) + eps);
+    }
+    x[i] = xi;
+    m[i] = mi;
+    v[i] = vi;
+  }
+}
+
+__global__ void k_adam_tail(float *x, const float *g, float *m, float *v, long long start, long long n, float lr,
+                            float b1, float b2, float omb1, float omb2, float eps, float bc1, float bc2) {
+  const long long i = start + threadIdx.x;
+  if (i >= n) return;
+  m[i] = fmaf(b1, m[i], omb1 * g[i]);
+  v[i] = fmaf(b2, v[i], omb2 * g[i] * g[i]);
+  x[i] -= lr * (m[i] / bc1) / (sqrtf(v[i] / bc2) + eps);
+}
+
+}  // namespace
+
+cudaError_t launch_deform(const float *canon, const float *omega, const float *theta, const float *sigma,
+                          long long n, long long stride, int nb, const float *t, int F, float *out, unsigned *err,
+                          cudaStream_t st) {
+  const long long total = n * ((F + kFrameChunk - 1) / kFrameChunk);
+  if (total == 0) return cudaSuccess;
+  const long long blocks = std::min<long long>((total + 255) / 256, 152LL * 32);
+  k_deform<<<(unsigned)blocks, 256, 0, st>>>(canon, omega, theta, sigma, n, stride, nb, t, F, out, err);
+  return cudaGetLastError();
+}
+
+int loss_blocks_per_frame(long long per_frame) {
+  const long long per4 = per_frame / 4;
+  return (int)std::max(1LL, std::min(1024LL, (per4 + 8191) / 8192));
+}
+
+cudaError_t launch_loss(const float *pred, const float *meas, long long per_frame, int F, const float *scale,
+                        double *loss, float *resid, double *partials, int bpf, cudaStream_t st) {
+  if (F == 0) return cudaSuccess;
+  dim3 grid(bpf, F);
+  k_loss_partial<<<grid, 256, 0, st>>>(reinterpret_cast<const float4 *>(pred),
+                                       reinterpret_cast<const float4 *>(meas), per_frame / 4, scale,
+                                       reinterpret_cast<float4 *>(resid), partials);
+  cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess || loss == nullptr) return e;
+  k_loss_final<<<F, 32, 0, st>>>(partials, bpf, loss);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_adam(float *x, const float *g, float *m, float *v, long long n, float lr, float b1, float b2,
+                        float omb1, float omb2, float eps, float bc1, float bc2, cudaStream_t st) {
+  const long long n4 = n / 4;
+  if (n4 > 0) {
+    const long long blocks = std::min<long long>((n4 + 255) / 256, 152LL * 16);
+    k_adam<<<(unsigned)blocks, 256, 0, st>>>(reinterpret_cast<float4 *>(x), reinterpret_cast<const float4 *>(g),
+                                             reinterpret_cast<float4 *>(m), reinterpret_cast<float4 *>(v), n4, lr,
+                                             b1, b2, omb1, omb2, eps, bc1, bc2);
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
+  }
+  if (n4 * 4 < n) {
+    k_adam_tail<<<1, 4, 0, st>>>(x, g, m, v, n4 * 4, n, lr, b1, b2, omb1, omb2, eps, bc1, bc2);
+    return cudaGetLastError();
+  }
+  return cudaSuccess;
+}
+
+}  // namespace pa

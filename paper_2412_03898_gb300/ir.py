@@ -1,0 +1,164 @@
+"""Iterative reconstruction (IR) driver of 4D SlingBAG on the library's
+kernels (Sec. 2.2, Fig. 2 stage 2; hyper-parameters of Sec. 3.2).
+
+One IR iteration: deform every frame (Eq. 1-2) -> forward projection of all
+frames -> per-frame FP64 L2 loss and residual -> 4D adjoint (states
+recomputed in-kernel) -> Adam on each parameter group with the paper's
+learning rates and step decay (step_size 160, drop 0.1).  The optimiser type
+is not named in the paper; Adam is this library's reading.
+
+Two execution forms of the same iteration:
+  - batched: all frames in one launch per kernel; the launch sequence of the
+    deform/forward/loss/adjoint part is captured once in a CUDA graph and
+    replayed (step_graph);
+  - per-frame: F plain launch sequences, one frame each, gradients
+    accumulated across frames (step_per_frame).
+"""
+from __future__ import annotations
+
+import math
+from typing import Optional
+
+import torch
+
+from . import Geometry, adam_step, adjoint, deform_balls, forward, residual_loss
+
+# Sec. 3.2: initial learning rates and step decay.
+LR_COORD = 5e-7
+LR_PRESSURE = 5e-4
+LR_STD = 5e-7
+LR_DEFORM = 5e-6
+STEP_SIZE = 160
+DROP_RATE = 0.1
+
+
+class GGBallIR:
+    """Parameters, gradients, optimiser state and preallocated buffers of one
+    4D reconstruction.
+
+    canon: [5, stride] (x, y, z, a, p); deform: [3, 5, Nb, stride] holding
+    omega, theta, sigma; t_frames: [F]; meas: [F, S, T]."""
+
+    def __init__(self, geom: Geometry, canon: torch.Tensor, deform: torch.Tensor, t_frames: torch.Tensor,
+                 meas: torch.Tensor, n: Optional[int] = None):
+        self.geom = geom
+        self.canon = canon
+        self.deform = deform
+        self.t = t_frames
+        self.meas = meas
+        self.n = canon.shape[-1] if n is None else int(n)
+        self.F = int(t_frames.numel())
+        dev = canon.device
+        self.g_canon = torch.zeros_like(canon)
+        self.g_deform = torch.zeros_like(deform)
+        self.m_canon, self.v_canon = torch.zeros_like(canon), torch.zeros_like(canon)
+        self.m_deform, self.v_deform = torch.zeros_like(deform), torch.zeros_like(deform)
+        stride = canon.shape[-1]
+        self.state = torch.empty(self.F, 5, stride, dtype=torch.float32, device=dev)
+        self.traces = torch.empty(self.F, geom.n_sensors, geom.n_samples, dtype=torch.float32, device=dev)
+        self.resid = torch.empty_like(self.traces)
+        self.loss = torch.empty(self.F, dtype=torch.float64, device=dev)
+        self.step_count = 0
+        self.graph: Optional[torch.cuda.CUDAGraph] = None
+        self._fws = None
+        self._lws = torch.empty(1 << 20, dtype=torch.uint8, device=dev)
+
+    # -- pieces ---------------------------------------------------------------
+    def _omega(self):
+        return self.deform[0]
+
+    def _grads_tuple(self):
+        return (self.g_canon, self.g_deform[0], self.g_deform[1], self.g_deform[2])
+
+    def _forward_loss_adjoint(self):
+        deform_balls(self.canon, self.deform[0], self.deform[1], self.deform[2], self.t, self.n, out=self.state)
+        forward(self.geom, self.state, self.n, out=self.traces, workspace=self._fws)
+        residual_loss(self.traces, self.meas, want_loss=True, want_resid=True, loss_out=self.loss,
+                      resid_out=self.resid, workspace=self._lws)
+        adjoint(self.geom, self.resid, canon=self.canon, omega=self.deform[0], theta=self.deform[1],
+                sigma=self.deform[2], t_frames=self.t, n=self.n, out=self._grads_tuple())
+
+    def lr_scale(self) -> float:
+        return DROP_RATE ** (self.step_count // STEP_SIZE)
+
+    def _adam(self):
+        self.step_count += 1
+        k = self.lr_scale()
+        stride = self.canon.shape[-1]
+        # x, y, z and a rows share one launch when their rates agree (both 5e-7)
+        assert LR_COORD == LR_STD
+        adam_step(self.canon[:4].view(-1), self.g_canon[:4].reshape(-1), self.m_canon[:4].view(-1),
+                  self.v_canon[:4].view(-1), LR_COORD * k, self.step_count)
+        adam_step(self.canon[4], self.g_canon[4], self.m_canon[4], self.v_canon[4], LR_PRESSURE * k, self.step_count)
+        adam_step(self.deform.view(-1), self.g_deform.view(-1), self.m_deform.view(-1), self.v_deform.view(-1),
+                  LR_DEFORM * k, self.step_count)
+        del stride
+
+    def _ensure_workspace(self):
+        from . import forward_workspace_size
+        need = forward_workspace_size(self.geom, self.state, self.n)
+        if need > 0 and (self._fws is None or self._fws.numel() < need):
+            self._fws = torch.empty(need, dtype=torch.uint8, device=self.canon.device)
+
+    # -- iteration forms -------------------------------------------------------
+    def step(self) -> torch.Tensor:
+        """One batched IR iteration with plain launches."""
+        self._ensure_workspace()
+        self._forward_loss_adjoint()
+        self._adam()
+        return self.loss
+
+    def capture(self) -> None:
+        """Capture the deform/forward/loss/adjoint launches in a CUDA graph."""
+        self._ensure_workspace()
+        s = torch.cuda.Stream()
+        s.wait_stream(torch.cuda.current_stream())
+        with torch.cuda.stream(s):
+            self._forward_loss_adjoint()  # warm-up on the capture stream
+        torch.cuda.current_stream().wait_stream(s)
+        g = torch.cuda.CUDAGraph()
+        with torch.cuda.graph(g):
+            self._forward_loss_adjoint()
+        self.graph = g
+
+    def step_graph(self) -> torch.Tensor:
+        """One batched IR iteration: graph replay + Adam."""
+        if self.graph is None:
+            self.capture()
+        self.graph.replay()
+        self._adam()
+        return self.loss
+
+    def step_per_frame(self) -> torch.Tensor:
+        """The same iteration as F plain single-frame launch sequences."""
+        self._ensure_workspace()
+        for f in range(self.F):
+            tf = self.t[f:f + 1]
+            st = self.state[f:f + 1]
+            deform_balls(self.canon, self.deform[0], self.deform[1], self.deform[2], tf, self.n, out=st)
+            forward(self.geom, st, self.n, out=self.traces[f:f + 1], workspace=self._fws)
+            residual_loss(self.traces[f:f + 1], self.meas[f:f + 1], want_loss=True, want_resid=True,
+                          loss_out=self.loss[f:f + 1], resid_out=self.resid[f:f + 1], workspace=self._lws)
+            adjoint(self.geom, self.resid[f:f + 1], canon=self.canon, omega=self.deform[0], theta=self.deform[1],
+                    sigma=self.deform[2], t_frames=tf, n=self.n, out=self._grads_tuple(), accumulate=f > 0)
+        self._adam()
+        return self.loss
+
+    def launches_per_step(self, per_frame: bool = False) -> int:
+        from . import forward_plan
+        p = forward_plan(self.geom, self.state[:1] if per_frame else self.state, self.n)
+        fwd = 1 + (1 if p["n_splits"] > 1 else 0)
+        core = 1 + fwd + 2 + 1  # deform, forward(+split reduce), loss partial+final, adjoint
+        adam = 3
+        return (core * self.F if per_frame else core) + adam
+
+
+def init_deformation(n_basis: int, stride: int, device, omega_scale: float = 0.0, seed: int = 0) -> torch.Tensor:
+    """Deformation parameters [3, 5, Nb, stride]: omega (zero, or small random
+    weights), theta evenly spaced on [0, 1], sigma = 1/Nb."""
+    g = torch.Generator(device="cpu").manual_seed(seed)
+    d = torch.empty(3, 5, n_basis, stride, dtype=torch.float32)
+    d[0] = torch.randn(5, n_basis, stride, generator=g) * omega_scale / math.sqrt(max(n_basis, 1))
+    d[1] = torch.linspace(0.0, 1.0, n_basis).view(1, n_basis, 1) if n_basis > 1 else 0.0
+    d[2] = 1.0 / n_basis
+    return d.to(device)

@@ -1,0 +1,66 @@
+"""Host-side checks of the C-ABI library that need no GPU: it builds, loads,
+exports every entry point include/pa.h declares, and rejects invalid
+arguments before touching the device."""
+import ctypes
+import os
+import re
+
+import pytest
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+def _declared():
+    src = open(os.path.join(ROOT, "include", "pa.h")).read()
+    return sorted(set(re.findall(r"PA_API\s+[\w\s\*]*?\b(pa_\w+)\s*\(", src)))
+
+
+@pytest.fixture(scope="module")
+def lib():
+    from paper_2412_03898_gb300 import build
+    build.build()
+    from paper_2412_03898_gb300 import _lib
+    return _lib.load()
+
+
+def test_header_declares_the_hot_path():
+    names = _declared()
+    for must in ("pa_deform_balls", "pa_forward", "pa_adjoint", "pa_residual_loss"):
+        assert must in names
+
+
+def test_library_exports_every_declared_symbol(lib):
+    for name in _declared():
+        assert hasattr(lib, name), name
+
+
+def test_binding_covers_the_header(lib):
+    from paper_2412_03898_gb300 import _lib
+    assert sorted(_lib.exported_symbols()) == _declared()
+
+
+def test_status_strings_and_version(lib):
+    assert lib.pa_version() >= 100
+    assert b"INVALID" in lib.pa_status_string(1)
+    assert b"DOMAIN" in lib.pa_status_string(2)
+
+
+def test_invalid_geometry_rejected_on_host(lib):
+    from paper_2412_03898_gb300 import _lib
+    g = _lib.pa_geom(None, 4, 4, 1.5, 40.0, 0.0, 64, 5.0)  # NULL sensors
+    b = _lib.pa_balls(None, 0, 0)
+    assert lib.pa_forward(ctypes.byref(g), ctypes.byref(b), 1, None, 0, None, 0, None) == _lib.PA_ERR_INVALID_ARG
+    g2 = _lib.pa_geom(16, 4, 4, 1.5, 40.0, 0.0, 62, 5.0)  # T % 4 != 0 (pointer never dereferenced)
+    assert lib.pa_forward(ctypes.byref(g2), ctypes.byref(b), 1, None, 0, None, 0, None) == _lib.PA_ERR_INVALID_ARG
+    g3 = _lib.pa_geom(16, 4, 4, 1.5, 40.0, 0.0, 64, 9.0)  # kappa out of range
+    assert lib.pa_forward(ctypes.byref(g3), ctypes.byref(b), 1, None, 0, None, 0, None) == _lib.PA_ERR_INVALID_ARG
+    b2 = _lib.pa_balls(16, 10, 10)  # stride not a multiple of 4
+    g4 = _lib.pa_geom(16, 4, 4, 1.5, 40.0, 0.0, 64, 5.0)
+    assert lib.pa_forward(ctypes.byref(g4), ctypes.byref(b2), 1, None, 0, None, 0, None) == _lib.PA_ERR_INVALID_ARG
+
+
+def test_invalid_loss_and_adam_args_rejected_on_host(lib):
+    from paper_2412_03898_gb300 import _lib
+    assert lib.pa_residual_loss(None, None, 6, 1, None, None, None, None, 0, None) == _lib.PA_ERR_INVALID_ARG
+    assert lib.pa_adam_step(None, None, None, None, 8, 1e-3, 0.9, 0.999, 1e-8, 0, None) == _lib.PA_ERR_INVALID_ARG
+    assert lib.pa_loss_workspace_size(0, 1) == 0
