@@ -198,6 +198,26 @@ PA_API int32_t pa_residual_loss(const float *pred, const float *meas, int64_t pe
                          const float *frame_scale, double *loss, float *resid, void *workspace,
                          size_t workspace_bytes, void *stream);
 
+/* pa_residual_loss without a workspace argument, for callers that cannot
+ * allocate device memory where they call it: a plugin whose host application
+ * owns every device allocation, or a C caller with no allocator at hand that
+ * must not call cudaMalloc (which can implicitly synchronise the device).
+ * The paper has no counterpart; this is a deployment variant of the loss.
+ * Same arguments, results and determinism as pa_residual_loss.  Its scratch
+ * is a fixed 128 KiB array inside the library, held on every GPU that loads
+ * the library until the process exits, with room for 16384 (frame, block)
+ * partial sums; a frame of P samples takes min(1024, ceil(P / 32768)) blocks
+ * (for example, up to 224 frames of 576 x 4096 samples).  Larger problems
+ * return PA_ERR_WORKSPACE without launching anything.  It allocates nothing.
+ * The first call on a device looks up that array's device address (with the
+ * device current) and caches it; make that first call before any stream
+ * capture.  All calls share the one array: calls that overlap on the GPU
+ * (two streams or two threads) race and must be serialised by the caller.
+ * Each call writes every partial it reads, so the array never needs
+ * clearing. */
+PA_API int32_t pa_residual_loss_noalloc(const float *pred, const float *meas, int64_t per_frame, int32_t n_frames,
+                                        const float *frame_scale, double *loss, float *resid, void *stream);
+
 /* Sum of squares in FP64 of a device float array (gradient norms), written to
  * *out (device double).  n % 4 == 0, x 16-byte aligned. */
 PA_API int32_t pa_sumsq(const float *x, int64_t n, double *out, void *workspace, size_t workspace_bytes,

@@ -79,6 +79,7 @@ def load() -> ctypes.CDLL:
         "pa_adjoint": (i32, [G, B, C, P, i32, P, P, GR, u32, P]),
         "pa_loss_workspace_size": (sz, [i64, i32]),
         "pa_residual_loss": (i32, [P, P, i64, i32, P, P, P, P, sz, P]),
+        "pa_residual_loss_noalloc": (i32, [P, P, i64, i32, P, P, P, P]),
         "pa_sumsq": (i32, [P, i64, P, P, sz, P]),
         "pa_count_contributions": (i32, [G, B, i32, P, P]),
         "pa_adam_step": (i32, [P, P, P, P, i64, ctypes.c_double, ctypes.c_double, ctypes.c_double, ctypes.c_double, i32, P]),
@@ -107,4 +108,4 @@ def exported_symbols() -> list[str]:
     """Names of the C-ABI entry points declared in this module."""
     return ["pa_status_string", "pa_version", "pa_device_error", "pa_deform_balls", "pa_forward_workspace_size",
             "pa_forward_workspace_size_ex", "pa_forward", "pa_forward_ex", "pa_forward_plan_info", "pa_adjoint",
-            "pa_loss_workspace_size", "pa_residual_loss", "pa_sumsq", "pa_count_contributions", "pa_adam_step"]
+            "pa_loss_workspace_size", "pa_residual_loss", "pa_residual_loss_noalloc", "pa_sumsq", "pa_count_contributions", "pa_adam_step"]
