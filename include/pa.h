@@ -153,21 +153,22 @@ PA_API int32_t pa_forward(const pa_geom *geom, const pa_balls *balls, int32_t n_
                    uint32_t flags, void *workspace, size_t workspace_bytes, void *stream);
 
 /* pa_forward with an explicit tile plan, for autotuning.  tiles = {sensors
- * per CTA (1..32, 0 = default), samples per CTA (multiple of 4, 0 = default),
+ * per CTA (1..16, 0 = default), samples per CTA (multiple of 4, 0 = default),
  * balls per TMA stage (multiple of 4, 0 = default), ball splits (0 =
- * default)}, host array, or NULL for the built-in heuristic.  Results are
- * identical to pa_forward up to float summation order across splits. */
+ * default), pairs swept together per warp (1, 2, 4 or 8; 0 = default)}, a
+ * host array of 5, or NULL for the built-in heuristic.  Results equal
+ * pa_forward's up to float summation order. */
 PA_API size_t pa_forward_workspace_size_ex(const pa_geom *geom, const pa_balls *balls, int32_t n_frames,
                                            const int32_t *tiles);
 PA_API int32_t pa_forward_ex(const pa_geom *geom, const pa_balls *balls, int32_t n_frames, float *traces,
                              uint32_t flags, const int32_t *tiles, void *workspace, size_t workspace_bytes,
                              void *stream);
 
-/* The plan pa_forward_ex would use: out6 (host) receives {sensors per CTA,
- * samples per CTA, balls per stage, ball splits, CTAs launched, dynamic
- * shared memory bytes per CTA}. */
+/* The plan pa_forward_ex would use: out7 (host) receives {sensors per CTA,
+ * samples per CTA, balls per stage, ball splits, pairs per sweep, CTAs
+ * launched, dynamic shared memory bytes per CTA}. */
 PA_API int32_t pa_forward_plan_info(const pa_geom *geom, const pa_balls *balls, int32_t n_frames,
-                                    const int32_t *tiles, int32_t *out6);
+                                    const int32_t *tiles, int32_t *out7);
 
 /* Adjoint of pa_forward (gradients of the L2 loss, Sec. 2.2, last paragraph:
  * all baseline attributes and all (theta, sigma, omega) are learnable).

@@ -152,8 +152,8 @@ def deform_balls(canon: torch.Tensor, omega: torch.Tensor, theta: torch.Tensor, 
 def _tiles(tiles: Optional[Sequence[int]]):
     if tiles is None:
         return None
-    arr = (ctypes.c_int32 * 4)(*[int(v) for v in tiles])
-    return arr
+    vals = [int(v) for v in tiles] + [0] * (5 - len(tiles))
+    return (ctypes.c_int32 * 5)(*vals[:5])
 
 
 def forward_workspace_size(geom: Geometry, state: torch.Tensor, n: Optional[int] = None,
@@ -167,10 +167,11 @@ def forward_workspace_size(geom: Geometry, state: torch.Tensor, n: Optional[int]
 def forward_plan(geom: Geometry, state: torch.Tensor, n: Optional[int] = None,
                  tiles: Optional[Sequence[int]] = None) -> dict:
     state, bs, n = _balls_struct(state, n)
-    out = (ctypes.c_int32 * 6)()
+    out = (ctypes.c_int32 * 7)()
     _lib.check(_LIB.pa_forward_plan_info(ctypes.byref(geom.struct()), ctypes.byref(bs), int(state.shape[0]),
                                          _tiles(tiles), out), "pa_forward_plan_info")
-    return dict(s_tile=out[0], t_tile=out[1], nb_tile=out[2], n_splits=out[3], ctas=out[4], smem=out[5])
+    return dict(s_tile=out[0], t_tile=out[1], nb_tile=out[2], n_splits=out[3], group=out[4], ctas=out[5],
+                smem=out[6])
 
 
 def forward(geom: Geometry, state: torch.Tensor, n: Optional[int] = None, out: Optional[torch.Tensor] = None,

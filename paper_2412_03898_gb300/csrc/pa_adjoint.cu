@@ -6,11 +6,13 @@
 // Design (GB300, sm_103a): ball-major, no atomics.
 //  - One warp owns one ball (static mode: one (frame, ball) item) and loops
 //    over all sensors.  The 32 lanes compute the window, phase and gradient
-//    factors of 32 (ball, sensor) pairs in parallel and publish them in
-//    shared memory; the warp then walks each pair's window with lanes on
-//    consecutive samples, reading the residual g[f][s][k] (coalesced, L2
-//    resident) and accumulating per lane
-//        S1 = sum g E u,  S3 = sum g E u (-u^2),  SR = sum g E (1 - tau^2/a^2)
+//    factors of 32 (ball, sensor) pairs in parallel and publish them,
+//    compacted, in shared memory; the warp then walks the windows of
+//    kAdjGroup pairs at a time in lockstep with lanes on consecutive samples,
+//    so that kAdjGroup independent coalesced residual loads g[f][s][k] (L2
+//    resident) are in flight per step, and accumulates per lane and pair
+//        S1 = sum g E u,  S3 = sum g E u^3,  SR = sum g E (1 - tau^2/a^2)
+//    (two sensors per packed FP32x2 instruction)
 //    which the per-pair factors fold into per-lane gradient accumulators.
 //  - A warp-shuffle reduction over lanes (i.e. over sensors and samples) at
 //    the end of the ball gives dL/d(x, y, z, a, p); one lane writes it.
@@ -21,7 +23,7 @@
 // Derivatives used, for v = A tau E, A = p/(2R), E = exp(-tau^2/(2a^2)),
 // tau = R - c t_k, u = tau s, s = K_S/a (so E = 2^(-u^2)):
 //   dv/dp = tau E/(2R)                     -> gp += S1 * a/(2 R K_S)
-//   dv/da = A tau^3 E / a^3                -> ga += S3 * (-A/K_S^3)
+//   dv/da = A tau^3 E / a^3                -> ga += S3 * A/K_S^3
 //   dv/dR = -A tau E/R + A E (1 - tau^2/a^2) -> dR = S1 * (-A a/(R K_S)) + A SR
 //   dR/dmu = (mu - x_s)/R.
 #include <algorithm>
@@ -34,11 +36,16 @@ namespace {
 
 constexpr int kAdjWarps = 8;
 
+// Pairs walked together per warp in the window loop: their residual loads are
+// independent, so G of them are in flight per warp and step.
+constexpr int kAdjGroup = 4;
+
 // dL/d(x, y, z, a, p) of one ball at frame f, summed over all sensors and
 // samples.  Returns the totals (identical in every lane).
 __device__ __forceinline__ void ball_frame_grad(const AdjArgs &A, const float *ssens, float4 *rec, int lane,
                                                 int f, float bx, float by, float bz, float a, float p,
                                                 float out[5], bool &dom) {
+  constexpr int G = kAdjGroup;
   const int S = A.q.S, T = A.q.T;
   float gx = 0.f, gy = 0.f, gz = 0.f, ga = 0.f, gp = 0.f;
   const float *gframe = A.g + (long long)f * S * T;
@@ -46,6 +53,7 @@ __device__ __forceinline__ void ball_frame_grad(const AdjArgs &A, const float *s
     for (int s0 = 0; s0 < S; s0 += 32) {
       const int s = s0 + lane;
       int W = 0;
+      float4 r0 = make_float4(0.f, 0.f, 0.f, 0.f), r1 = r0, r2 = r0;
       if (s < S) {
         const float sx = ssens[s], sy = ssens[S + s], sz = ssens[2 * S + s];
         const PairWin w = pair_window<false>(A.q, bx, by, bz, a, p, sx, sy, sz, 0, T - 1);
@@ -55,40 +63,81 @@ __device__ __forceinline__ void ball_frame_grad(const AdjArgs &A, const float *s
           const float invR = __fdividef(1.f, w.R);
           const float amp = 0.5f * p * invR;        // A = p/(2R)
           const float aK = a * (1.f / K_S);         // 1/s
-          rec[3 * lane + 0] = make_float4(w.u0, w.du, 0.5f * invR * aK, -amp * (1.f / (K_S * K_S * K_S)));
-          rec[3 * lane + 1] = make_float4(-amp * invR * aK, amp, (bx - sx) * invR, (by - sy) * invR);
-          rec[3 * lane + 2] = make_float4((bz - sz) * invR, __int_as_float(w.klo), __int_as_float(W),
-                                          __int_as_float(s));
+          r0 = make_float4(w.u0, w.du, 0.5f * invR * aK, -amp * (1.f / (K_S * K_S * K_S)));
+          r1 = make_float4(-amp * invR * aK, amp, (bx - sx) * invR, (by - sy) * invR);
+          r2 = make_float4((bz - sz) * invR, __int_as_float(w.klo), __int_as_float(W), __int_as_float(s));
         }
       }
-      unsigned mask = __ballot_sync(FULL, W > 0);
+      // compact the valid pairs to the front of the warp's record slots
+      const unsigned mask = __ballot_sync(FULL, W > 0);
+      const int nv = __popc(mask);
+      if (W > 0) {
+        const int pos = __popc(mask & ((1u << lane) - 1u));
+        rec[3 * pos + 0] = r0;
+        rec[3 * pos + 1] = r1;
+        rec[3 * pos + 2] = r2;
+      }
       __syncwarp();
-      while (mask) {
-        const int i = __ffs(mask) - 1;
-        mask &= mask - 1;
-        const float4 r0 = rec[3 * i + 0], r1 = rec[3 * i + 1], r2 = rec[3 * i + 2];
-        const int klo = __float_as_int(r2.y), Wi = __float_as_int(r2.z), si = __float_as_int(r2.w);
-        const float *g = gframe + (long long)si * T + klo;
-        float u = fmaf((float)lane, -r0.y, r0.x);
-        const float du32 = 32.f * r0.y;
-        float S1 = 0.f, S3 = 0.f, SR = 0.f;
-        for (int j = lane; j < Wi; j += 32) {
-          const float G = __ldg(g + j);
-          const float arg = -u * u;
-          const float E = ex2(arg);
-          const float ge = G * E;
-          const float gu = ge * u;
-          S1 += gu;
-          S3 = fmaf(gu, arg, S3);
-          SR = fmaf(ge, fmaf(arg, K_2LN2, 1.f), SR);
-          u -= du32;
+      for (int g0 = 0; g0 < nv; g0 += G) {
+        const float *gq[G];
+        int Wq[G];
+        int wmax = 0;
+        // pairs in twos: the per-sample arithmetic of two sensors shares one
+        // packed FP32x2 instruction
+        float2 u2[G / 2], nd2[G / 2], S1[G / 2], S3[G / 2], SR[G / 2];
+#pragma unroll
+        for (int q = 0; q < G; ++q) {
+          const bool act = g0 + q < nv;
+          const int i = act ? g0 + q : 0;
+          const float4 a0 = rec[3 * i + 0], a2 = rec[3 * i + 2];
+          Wq[q] = act ? __float_as_int(a2.z) : 0;
+          wmax = max(wmax, Wq[q]);
+          gq[q] = gframe + (long long)__float_as_int(a2.w) * T + __float_as_int(a2.y);
+          const float u = act ? fmaf((float)lane, -a0.y, a0.x) : 0.f;
+          const float nd = act ? -32.f * a0.y : 0.f;
+          if (q & 1) {
+            u2[q / 2].y = u;
+            nd2[q / 2].y = nd;
+          } else {
+            u2[q / 2].x = u;
+            nd2[q / 2].x = nd;
+          }
         }
-        gp = fmaf(S1, r0.z, gp);
-        ga = fmaf(S3, r0.w, ga);
-        const float dR = fmaf(S1, r1.x, r1.y * SR);
-        gx = fmaf(dR, r1.z, gx);
-        gy = fmaf(dR, r1.w, gy);
-        gz = fmaf(dR, r2.x, gz);
+#pragma unroll
+        for (int h = 0; h < G / 2; ++h) S1[h] = S3[h] = SR[h] = make_float2(0.f, 0.f);
+        const float2 negk = make_float2(-K_2LN2, -K_2LN2), one = make_float2(1.f, 1.f);
+        for (int j = lane; j - lane < wmax; j += 32) {
+          float Gv[G];
+#pragma unroll
+          for (int q = 0; q < G; ++q) Gv[q] = j < Wq[q] ? __ldg(gq[q] + j) : 0.f;
+#pragma unroll
+          for (int h = 0; h < G / 2; ++h) {
+            const float2 sq = __fmul2_rn(u2[h], u2[h]);                       // u^2
+            const float2 E = make_float2(ex2(-sq.x), ex2(-sq.y));             // exp(-tau^2/(2a^2))
+            const float2 ge = __fmul2_rn(make_float2(Gv[2 * h], Gv[2 * h + 1]), E);
+            const float2 gu = __fmul2_rn(ge, u2[h]);
+            S1[h] = __fadd2_rn(S1[h], gu);                                    // sum g E u
+            S3[h] = __ffma2_rn(gu, sq, S3[h]);                                // sum g E u^3
+            SR[h] = __ffma2_rn(ge, __ffma2_rn(sq, negk, one), SR[h]);         // sum g E (1 - tau^2/a^2)
+            u2[h] = __fadd2_rn(u2[h], nd2[h]);
+          }
+        }
+#pragma unroll
+        for (int q = 0; q < G; ++q) {
+          if (g0 + q < nv) {
+            const int i = g0 + q;
+            const float4 a0 = rec[3 * i + 0], a1 = rec[3 * i + 1], a2 = rec[3 * i + 2];
+            const float s1 = (q & 1) ? S1[q / 2].y : S1[q / 2].x;
+            const float s3 = (q & 1) ? S3[q / 2].y : S3[q / 2].x;
+            const float sr = (q & 1) ? SR[q / 2].y : SR[q / 2].x;
+            gp = fmaf(s1, a0.z, gp);
+            ga = fmaf(s3, -a0.w, ga);  // record holds -A/K_S^3 for sum g E u (-u^2)
+            const float dR = fmaf(s1, a1.x, a1.y * sr);
+            gx = fmaf(dR, a1.z, gx);
+            gy = fmaf(dR, a1.w, gy);
+            gz = fmaf(dR, a2.x, gz);
+          }
+        }
       }
       __syncwarp();
     }

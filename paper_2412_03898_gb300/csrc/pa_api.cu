@@ -101,12 +101,12 @@ int forward_impl(const pa_geom *geom, const pa_balls *balls, int32_t F, float *t
     return cuda_status(
         cudaMemsetAsync(traces, 0, sizeof(float) * (size_t)F * geom->n_sensors * geom->n_samples, st));
   }
-  if (tiles && (tiles[0] < 0 || tiles[0] > 32 || tiles[1] < 0 || tiles[2] < 0 || tiles[3] < 0 ||
-                (tiles[2] & 3) != 0 || (tiles[1] & 3) != 0))
+  if (tiles && (tiles[0] < 0 || tiles[0] > 16 || tiles[1] < 0 || tiles[2] < 0 || tiles[3] < 0 ||
+                (tiles[2] & 3) != 0 || (tiles[1] & 3) != 0 || tiles[4] < 0 || tiles[4] > 8))
     return PA_ERR_INVALID_ARG;
   const pa::FwdPlan p = pa::forward_plan(geom->n_sensors, geom->n_samples, balls->n, F, d->sms,
                                          tiles ? tiles[0] : 0, tiles ? tiles[1] : 0, tiles ? tiles[2] : 0,
-                                         tiles ? tiles[3] : 0);
+                                         tiles ? tiles[3] : 0, tiles ? tiles[4] : 0);
   if ((int)p.smem > d->max_smem) return PA_ERR_INVALID_ARG;
   if (p.ws_bytes > 0 && (ws == nullptr || ws_bytes < p.ws_bytes || !aligned(ws, 256))) return PA_ERR_WORKSPACE;
   pa::FwdArgs a;
@@ -183,7 +183,7 @@ size_t pa_forward_workspace_size_ex(const pa_geom *geom, const pa_balls *balls, 
   if (!d) return 0;
   const pa::FwdPlan p = pa::forward_plan(geom->n_sensors, geom->n_samples, balls->n, n_frames, d->sms,
                                          tiles ? tiles[0] : 0, tiles ? tiles[1] : 0, tiles ? tiles[2] : 0,
-                                         tiles ? tiles[3] : 0);
+                                         tiles ? tiles[3] : 0, tiles ? tiles[4] : 0);
   return p.ws_bytes;
 }
 
@@ -202,8 +202,9 @@ int32_t pa_forward_ex(const pa_geom *geom, const pa_balls *balls, int32_t n_fram
 }
 
 int32_t pa_forward_plan_info(const pa_geom *geom, const pa_balls *balls, int32_t n_frames, const int32_t *tiles,
-                             int32_t *out6) {
-  if (out6 == nullptr) return PA_ERR_INVALID_ARG;
+                             int32_t *out7) {
+  if (out7 == nullptr) return PA_ERR_INVALID_ARG;
+  if (tiles && (tiles[0] < 0 || tiles[0] > 16 || tiles[4] < 0 || tiles[4] > 8)) return PA_ERR_INVALID_ARG;
   int rc = check_geom(geom);
   if (rc) return rc;
   if ((rc = check_balls(balls))) return rc;
@@ -212,13 +213,14 @@ int32_t pa_forward_plan_info(const pa_geom *geom, const pa_balls *balls, int32_t
   if (!d) return PA_ERR_CUDA;
   const pa::FwdPlan p = pa::forward_plan(geom->n_sensors, geom->n_samples, balls->n, n_frames, d->sms,
                                          tiles ? tiles[0] : 0, tiles ? tiles[1] : 0, tiles ? tiles[2] : 0,
-                                         tiles ? tiles[3] : 0);
-  out6[0] = p.s_tile;
-  out6[1] = p.t_tile;
-  out6[2] = p.nb_tile;
-  out6[3] = p.n_splits;
-  out6[4] = (int32_t)((long long)n_frames * p.n_stiles * p.n_ttiles * p.n_splits);
-  out6[5] = (int32_t)p.smem;
+                                         tiles ? tiles[3] : 0, tiles ? tiles[4] : 0);
+  out7[0] = p.s_tile;
+  out7[1] = p.t_tile;
+  out7[2] = p.nb_tile;
+  out7[3] = p.n_splits;
+  out7[4] = p.group;
+  out7[5] = (int32_t)((long long)n_frames * p.n_stiles * p.n_ttiles * p.n_splits);
+  out7[6] = (int32_t)p.smem;
   return PA_OK;
 }
 

@@ -156,6 +156,22 @@ __device__ __forceinline__ double warp_sum_d(double v) {
   return v;
 }
 
+// Sorts distinct unsigned keys across the 32 lanes of a warp, ascending
+// (bitonic network on shuffles).  Callers pack the lane index into the low
+// bits, which makes the keys distinct and carries the payload.
+__device__ __forceinline__ unsigned warp_sort(unsigned key, int lane) {
+#pragma unroll
+  for (int k = 2; k <= 32; k <<= 1) {
+#pragma unroll
+    for (int j = k >> 1; j > 0; j >>= 1) {
+      const unsigned other = __shfl_xor_sync(FULL, key, j);
+      const bool keep_min = ((lane & j) == 0) == ((lane & k) == 0);
+      key = keep_min ? min(key, other) : max(key, other);
+    }
+  }
+  return key;
+}
+
 // ---------------------------------------------------------------------------
 // Acquisition scalars prepared on the host in double precision and split
 // into float pairs: delta = c/fs (distance per sample) and ct0 = c*t0.
@@ -171,7 +187,7 @@ struct Acq {
 
 // Parameters of one (ball, sensor) pair on a sample range [k_begin, k_end].
 struct PairWin {
-  float u0;   // scaled tau at k_lo: u = tau * K_S / a (tau itself for the uniform profile)
+  float u0;   // scaled tau at k_lo: u = tau * K_S / a (tau / a for the uniform profile)
   float du;   // decrement of u per sample
   float amp;  // p / (2 R s): v = amp * u * 2^(-u^2)
   float R;    // distance (hi part)
@@ -220,10 +236,13 @@ __device__ __forceinline__ PairWin pair_window(const Acq &q, float bx, float by,
   const float pl = fmaf(klo_f, q.dh, -ph);
   const float t = __fsub_rn(rch, ph);
   const float tau0 = __fadd_rn(t, __fsub_rn(__fsub_rn(rcl, pl), __fmul_rn(klo_f, q.dl)));
-  const float s = UNIFORM ? 1.f : __fdiv_rn(K_S, a);
+  // u = tau s: the window is |u| <= kappa K_S (Gaussian) or |u| <= 1 (uniform)
+  // (an approximate quotient only rescales u and amp consistently: v keeps
+  // its amplitude and the Gaussian width changes by ~2^-22 relative)
+  const float s = UNIFORM ? __fdividef(1.f, a) : __fdividef(K_S, a);
   w.u0 = tau0 * s;
   w.du = q.dh * s;
-  w.amp = __fdiv_rn(p, 2.f * rh * s);
+  w.amp = __fdividef(p, 2.f * rh * s);
   w.klo = (int)klo_f;
   w.W = (int)khi_f - w.klo + 1;
   return w;

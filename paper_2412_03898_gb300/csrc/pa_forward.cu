@@ -10,10 +10,15 @@
 //    into shared memory by TMA bulk copies (cp.async.bulk) completing on
 //    mbarriers, double buffered, issued by one thread.
 //  - Per 32-ball chunk, the 32 lanes compute the window and phase of 32
-//    (ball, sensor) pairs in parallel (double-float distance, once per pair),
-//    publish them in shared memory, and then the warp walks each pair's
-//    arrival window with lanes on consecutive samples (conflict-free shared
-//    accesses): u -= 32 du; v = amp * u * 2^(-u^2); trace[k] += v.
+//    (ball, sensor) pairs in parallel (double-float distance, once per pair)
+//    and publish them in shared memory.  The warp sorts the pairs by first
+//    sample (bitonic network on shuffles) and sweeps groups of G consecutive
+//    pairs over the union of their windows: each lane owns one sample of a
+//    32-sample step, adds the G balls' pulses to it in a register
+//        u -= 32 du;  v = amp u 2^(-u^2)  if |u| <= kappa K_S
+//    and does one shared-memory load and store per sample and group.  Sorted
+//    groups overlap almost completely, so the sweep wastes few lanes while
+//    giving G independent dependency chains per step.
 //  - Trace tiles are flushed with coalesced float4 stores.  With more than
 //    one ball split, partial traces go to the workspace and a second kernel
 //    sums them in split order (deterministic).
@@ -25,10 +30,10 @@ namespace pa {
 
 namespace {
 
-constexpr int kMaxThreads = 1024;
+constexpr int kMaxThreads = 512;  // at most 16 sensors (warps) per CTA
 
-template <bool UNIFORM>
-__global__ void __launch_bounds__(kMaxThreads) k_forward(const FwdArgs A) {
+template <bool UNIFORM, int G>
+__global__ void __launch_bounds__(kMaxThreads, 1) k_forward(const FwdArgs A) {
   extern __shared__ __align__(128) unsigned char smem_raw[];
   uint64_t *bars = reinterpret_cast<uint64_t *>(smem_raw);
   float *sball = reinterpret_cast<float *>(smem_raw + 128);
@@ -90,6 +95,8 @@ __global__ void __launch_bounds__(kMaxThreads) k_forward(const FwdArgs A) {
   float *mytr = str + warp * A.t_tile;
   float4 *myrec = srec + warp * 32;
   bool dom = false;
+  // window bound in scaled units: |u| <= kappa K_S (Gaussian), |u| <= 1 (uniform)
+  const float umax2 = UNIFORM ? 1.f : (A.q.kappa * K_S) * (A.q.kappa * K_S);
 
   for (int t = 0; t < ntiles; ++t) {
     const int stage = t & 1;
@@ -99,6 +106,17 @@ __global__ void __launch_bounds__(kMaxThreads) k_forward(const FwdArgs A) {
       const float *bx = sball + stage * 5 * nbt;
       for (int c0 = 0; c0 < cnt; c0 += 32) {
         const int bi = c0 + lane;
+        // cheap FP32 estimate of the window: skip chunks with no pair in this tile
+        bool maybe = false;
+        if (bi < cnt) {
+          const float dx = bx[bi] - sx, dy = bx[nbt + bi] - sy, dz = bx[2 * nbt + bi] - sz;
+          const float a = bx[3 * nbt + bi];
+          const float h = (UNIFORM ? 1.f : A.q.kappa) * a;
+          const float rc = sqrtf(fmaf(dx, dx, fmaf(dy, dy, dz * dz))) - A.q.ct0h;
+          const float lo = (rc - h) * A.q.inv_delta, hi = (rc + h) * A.q.inv_delta;
+          maybe = a > 0.f && bx[4 * nbt + bi] != 0.f && hi >= (float)(k0 - 2) && lo <= (float)(k0 + klen + 1);
+        }
+        if (__ballot_sync(FULL, maybe) == 0) continue;
         PairWin w;
         w.W = 0;
         w.domain_err = false;
@@ -106,22 +124,65 @@ __global__ void __launch_bounds__(kMaxThreads) k_forward(const FwdArgs A) {
           w = pair_window<UNIFORM>(A.q, bx[bi], bx[nbt + bi], bx[2 * nbt + bi], bx[3 * nbt + bi],
                                    bx[4 * nbt + bi], sx, sy, sz, k0, k0 + klen - 1);
         dom |= w.domain_err;
-        if (w.W > 0) myrec[lane] = make_float4(w.u0, w.du, w.amp, __int_as_float((w.klo - k0) | (w.W << 16)));
-        unsigned mask = __ballot_sync(FULL, w.W > 0);
+        const bool valid = w.W > 0;
+        const int nv = __popc(__ballot_sync(FULL, valid));
+        if (nv == 0) continue;
+        if (valid) myrec[lane] = make_float4(w.u0, w.du, w.amp, __int_as_float((w.klo - k0) | (w.W << 16)));
+        // sort by first sample; invalid pairs last; lane index in the low bits
+        const unsigned key = warp_sort(((valid ? (unsigned)(w.klo - k0) : 0xffffu) << 5) | (unsigned)lane, lane);
         __syncwarp();
-        while (mask) {
-          const int i = __ffs(mask) - 1;
-          mask &= mask - 1;
-          const float4 r = myrec[i];
-          const int packed = __float_as_int(r.w);
-          const int kl = packed & 0xffff, W = packed >> 16;
-          float u = fmaf((float)lane, -r.y, r.x);
-          const float du32 = 32.f * r.y;
-          float *tr = mytr + kl;
-          for (int j = lane; j < W; j += 32) {
-            const float E = UNIFORM ? 1.f : ex2(-u * u);
-            tr[j] = fmaf(r.z * u, E, tr[j]);
-            u -= du32;
+        for (int g0 = 0; g0 < nv; g0 += G) {
+          float uq[G], duq[G], aq[G];
+          int klq[G];
+          int kmin = 0x7fffffff, kmax = -1;
+#pragma unroll
+          for (int q = 0; q < G; ++q) {
+            const int src = (int)(__shfl_sync(FULL, key, (g0 + q) & 31) & 31u);
+            const bool act = g0 + q < nv;
+            const float4 r = myrec[src];
+            const int pk = __float_as_int(r.w);
+            const int kl = pk & 0xffff, W = pk >> 16;
+            if (act) {
+              kmin = min(kmin, kl);
+              kmax = max(kmax, kl + W - 1);
+            }
+            // inactive slots: far outside every window, zero amplitude
+            uq[q] = act ? r.x : 1e30f;
+            duq[q] = act ? r.y : 0.f;
+            aq[q] = act ? r.z : 0.f;
+            klq[q] = act ? kl : 0;
+          }
+          // balls in twos: u, its step and amp*u of two balls share one packed
+          // FP32x2 instruction.  u starts at this lane's first sample
+          // kmin + lane; the offset from the pair's own first sample is a small
+          // exact integer.
+          float2 u2[(G + 1) / 2], nd2[(G + 1) / 2], amp2[(G + 1) / 2];
+#pragma unroll
+          for (int h = 0; h < (G + 1) / 2; ++h) {
+            const int q0 = 2 * h, q1 = min(2 * h + 1, G - 1);
+            const bool has1 = 2 * h + 1 < G;
+            u2[h] = make_float2(fmaf((float)(kmin + lane - klq[q0]), -duq[q0], uq[q0]),
+                                has1 ? fmaf((float)(kmin + lane - klq[q1]), -duq[q1], uq[q1]) : 1e30f);
+            nd2[h] = make_float2(-32.f * duq[q0], has1 ? -32.f * duq[q1] : 0.f);
+            amp2[h] = make_float2(aq[q0], has1 ? aq[q1] : 0.f);
+          }
+          for (int base = kmin; base <= kmax; base += 32) {
+            const int k = base + lane;
+            if (k <= kmax) {
+              float t = mytr[k];
+#pragma unroll
+              for (int h = 0; h < (G + 1) / 2; ++h) {
+                const float2 sq = __fmul2_rn(u2[h], u2[h]);
+                const float2 w = __fmul2_rn(amp2[h], u2[h]);
+                const float ex = UNIFORM ? 1.f : ex2(-sq.x);
+                const float ey = UNIFORM ? 1.f : ex2(-sq.y);
+                if (sq.x <= umax2) t = fmaf(w.x, ex, t);
+                if (sq.y <= umax2) t = fmaf(w.y, ey, t);
+              }
+              mytr[k] = t;
+            }
+#pragma unroll
+            for (int h = 0; h < (G + 1) / 2; ++h) u2[h] = __fadd2_rn(u2[h], nd2[h]);
           }
           __syncwarp();
         }
@@ -212,24 +273,39 @@ size_t forward_smem_bytes(int s_tile, int t_tile, int nb_tile) {
          sizeof(float) * (size_t)s_tile * t_tile;
 }
 
+namespace {
+using FwdKernel = void (*)(const FwdArgs);
+FwdKernel forward_kernel(bool uniform, int group) {
+  if (uniform) return k_forward<true, 4>;
+  switch (group) {
+    case 1: return k_forward<false, 1>;
+    case 2: return k_forward<false, 2>;
+    case 4: return k_forward<false, 4>;
+    default: return k_forward<false, 8>;
+  }
+}
+}  // namespace
+
 int forward_blocks_per_sm(const FwdPlan &p, bool uniform) {
   int nb = 0;
-  auto fn = uniform ? k_forward<true> : k_forward<false>;
+  auto fn = forward_kernel(uniform, p.group);
   cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)p.smem);
   cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, fn, 32 * p.s_tile, p.smem);
   return nb;
 }
 
 FwdPlan forward_plan(int S, int T, long long n, int F, int sms, int s_tile_o, int t_tile_o,
-                     int nb_tile_o, int splits_o) {
+                     int nb_tile_o, int splits_o, int group_o) {
   FwdPlan p{};
-  p.s_tile = s_tile_o > 0 ? s_tile_o : 8;
-  // Whole trace per CTA when it fits comfortably, else 2048-sample tiles.
-  int tt = t_tile_o > 0 ? t_tile_o : (T <= 4096 ? T : 2048);
+  p.group = (group_o == 1 || group_o == 2 || group_o == 4) ? group_o : 8;
+  p.s_tile = s_tile_o > 0 ? s_tile_o : 16;
+  // 16 warps x 2048 samples per CTA measured best on the static 100k-ball
+  // workload (one 150 KB CTA per SM, 16 warps).
+  int tt = t_tile_o > 0 ? t_tile_o : 2048;
   tt = std::min(std::min(tt, T), 16384);
   tt = (tt + 3) & ~3;
   p.t_tile = tt;
-  p.nb_tile = nb_tile_o > 0 ? nb_tile_o : 512;
+  p.nb_tile = nb_tile_o > 0 ? nb_tile_o : 256;
   p.n_stiles = (S + p.s_tile - 1) / p.s_tile;
   p.n_ttiles = (T + p.t_tile - 1) / p.t_tile;
   p.smem = forward_smem_bytes(p.s_tile, p.t_tile, p.nb_tile);
@@ -263,7 +339,7 @@ FwdPlan forward_plan(int S, int T, long long n, int F, int sms, int s_tile_o, in
 }
 
 cudaError_t launch_forward(const FwdArgs &a, const FwdPlan &p, bool uniform, cudaStream_t st) {
-  auto fn = uniform ? k_forward<true> : k_forward<false>;
+  auto fn = forward_kernel(uniform, p.group);
   cudaError_t e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)p.smem);
   if (e != cudaSuccess) return e;
   const long long grid = (long long)a.F * p.n_stiles * p.n_ttiles * p.n_splits;

@@ -15,6 +15,7 @@ struct FwdPlan {
   int t_tile;      // samples per CTA
   int nb_tile;     // balls per TMA stage
   int n_splits;    // ball-range splits (partial traces summed by a second kernel)
+  int group;       // pairs swept together per warp (1, 2, 4 or 8)
   int n_stiles, n_ttiles;
   long long balls_per_split;
   size_t smem;     // dynamic shared memory per CTA
@@ -55,7 +56,7 @@ struct AdjArgs {
 // Plan selection (tile sizes, splits); `override` entries > 0 replace the
 // heuristic (used by the autotuner).
 FwdPlan forward_plan(int S, int T, long long n, int F, int sms, int s_tile_override,
-                     int t_tile_override, int nb_tile_override, int splits_override);
+                     int t_tile_override, int nb_tile_override, int splits_override, int group_override);
 size_t forward_smem_bytes(int s_tile, int t_tile, int nb_tile);
 int forward_blocks_per_sm(const FwdPlan &p, bool uniform);
 

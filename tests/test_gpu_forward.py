@@ -26,7 +26,7 @@ def _oracle_traces(sc, state=None):
     return y, n
 
 
-@pytest.mark.parametrize("tiles", [None, (8, 256, 128, 3), (5, 1024, 64, 1), (32, 128, 512, 2), (1, 1028, 4, 7)])
+@pytest.mark.parametrize("tiles", [None, (8, 256, 128, 3, 4), (5, 1024, 64, 1, 1), (16, 128, 512, 2, 8), (1, 1028, 4, 7, 2)])
 def test_forward_parity_tiles(pa, tiles):
     sc = pa_inputs.small_scene(seed=1, n_balls=1003, n_sensors=37, n_samples=1028)
     geom = geometry(sc)
@@ -115,7 +115,7 @@ def test_invalid_arguments_are_rejected(pa):
     geom = geometry(sc)
     st = dev_pad(sc.balls)[None]
     with pytest.raises(pa.PAError):
-        pa.forward(geom, st, 10, tiles=(33, 0, 0, 0))
+        pa.forward(geom, st, 10, tiles=(17, 0, 0, 0))
     bad = pa.Geometry(geom.sensors, sc.c, sc.fs, sc.t0, 62, sc.kappa)  # T % 4 != 0
     with pytest.raises(pa.PAError):
         pa.forward(bad, st, 10)
