@@ -53,6 +53,9 @@ def parse():
     ap.add_argument("--no-4d", action="store_true", help="skip the 4D IR comparison")
     ap.add_argument("--no-cpu", action="store_true", help="skip the oracle cpu_baseline leg")
     ap.add_argument("--steps-4d", type=int, default=3)
+    ap.add_argument("--no-batched", action="store_true", help="skip the 16-scene batched comparison")
+    ap.add_argument("--steps-batched", type=int, default=2)
+    ap.add_argument("--no-autotune", action="store_true")
     a = ap.parse_args()
     a.warmup = max(a.warmup, 3)
     return a
@@ -236,8 +239,12 @@ def run_ours(args):
     meas = pa.forward(geom, to_dev(gt)[None].contiguous(), n)
     torch.cuda.synchronize()
     C = pa.count_contributions(geom, state, n)
-    plan = pa.forward_plan(geom, state, n)
-    fws = torch.empty(max(pa.forward_workspace_size(geom, state, n), 16), dtype=torch.uint8, device=dev)
+    tiles = None
+    if not args.no_autotune:
+        from paper_2412_03898_gb300.autotune import tune_forward
+        tiles = tune_forward(geom, state, n)  # set-up, not timed
+    plan = pa.forward_plan(geom, state, n, tiles=tiles)
+    fws = torch.empty(max(pa.forward_workspace_size(geom, state, n, tiles=tiles), 16), dtype=torch.uint8, device=dev)
     lws = torch.empty(1 << 20, dtype=torch.uint8, device=dev)
     traces = torch.empty(1, geom.n_sensors, geom.n_samples, device=dev)
     resid = torch.empty_like(traces)
@@ -249,7 +256,7 @@ def run_ours(args):
     def step(ev=None):
         if ev is not None:
             ev[0].record(stream)
-        pa.forward(geom, state, n, out=traces, workspace=fws)
+        pa.forward(geom, state, n, out=traces, workspace=fws, tiles=tiles)
         if ev is not None:
             ev[1].record(stream)
         pa.residual_loss(traces, meas, want_loss=True, want_resid=True, loss_out=loss, resid_out=resid,
@@ -312,6 +319,9 @@ def run_ours(args):
     ir4d = None
     if not args.no_4d:
         ir4d = bench_4d(args, pa, pa_inputs, dev, flush)
+    batched = None
+    if not args.no_batched:
+        batched = bench_batched(args, pa, pa_inputs, dev, flush)
     clocks = sampler.stop()
 
     fwd_avg = statistics.mean(t_fwd)
@@ -330,6 +340,7 @@ def run_ours(args):
         "config": {"workload": CONFIG_DESC, "n_balls": n, "n_sensors": geom.n_sensors,
                    "n_samples": geom.n_samples, "contributions_per_step": C,
                    "l2": "flushed (512 MB write) before every timed step", "forward_plan": plan,
+                   "forward_tiles": "autotuned" if tiles is not None else "default",
                    "parallelism": f"replicas x{world}"},
         "clocks": clocks,
         "e2e": {"value": world * C * args.steps / (e2e_ms * 1e-3), "unit": UNIT, "h2d_bytes_per_step": e2e_in,
@@ -344,6 +355,8 @@ def run_ours(args):
     }
     if ir4d is not None:
         line["ir4d"] = ir4d
+    if batched is not None:
+        line["batched"] = batched
     if rank == 0 and world == 1 and not args.no_cpu:
         line["cpu_baseline"] = cpu_baseline(sc)
     if rank == 0:
@@ -397,6 +410,76 @@ def bench_4d(args, pa, pa_inputs, dev, flush):
         del ir
     out["speedup_batched_vs_per_frame"] = res["batched_graph"] / res["per_frame"]
     out["contrib_per_s_batched"] = 2 * C * res["batched_graph"]
+    return out
+
+
+def bench_batched(args, pa, pa_inputs, dev, flush):
+    """16 uneven scenes (N log-uniform in [1e4, 5e5], S in {256, 576, 1024},
+    T in [2048, 4096], 1-10 frames): forward + static adjoint of all scenes
+    as two persistent launches replayed from one CUDA graph, vs plain
+    per-scene launches."""
+    import torch
+    from paper_2412_03898_gb300.autotune import tune_batched
+    raw = pa_inputs.config_scene(5)
+    to_dev = lambda a: pa.pad_last(torch.from_numpy(np.ascontiguousarray(a, dtype=np.float32)).to(dev))
+    scenes = []
+    C = 0
+    for sc in raw:
+        st = to_dev(sc.frames if sc.frames is not None else sc.balls[None]).contiguous()
+        geom = pa.Geometry(torch.from_numpy(sc.sensors).to(dev), sc.c, sc.fs, sc.t0, sc.n_samples, sc.kappa)
+        C += pa.count_contributions(geom, st, sc.n_balls)
+        b = pa.Scene(geom, st, sc.n_balls)
+        b.traces = torch.empty(b.F, geom.n_sensors, geom.n_samples, device=dev)
+        b.trace_grad = b.traces  # any residual: the work does not depend on its values
+        b.grad_state = torch.empty_like(st)
+        scenes.append(b)
+    tiles = tune_batched(scenes) if not args.no_autotune else None
+    ws = torch.empty(256, dtype=torch.uint8, device=dev)
+    ws2 = torch.empty(256, dtype=torch.uint8, device=dev)
+
+    def batched_step():
+        pa.forward_batched(scenes, tiles=tiles, workspace=ws)
+        pa.adjoint_batched(scenes, workspace=ws2)
+
+    per_ws = {}
+    for b in scenes:
+        need = pa.forward_workspace_size(b.geom, b.state, b.n)
+        per_ws[id(b)] = torch.empty(max(need, 16), dtype=torch.uint8, device=dev)
+
+    def per_scene_step():
+        for b in scenes:
+            pa.forward(b.geom, b.state, b.n, out=b.traces, workspace=per_ws[id(b)])
+            pa.adjoint(b.geom, b.trace_grad, state=b.state, n=b.n, out=b.grad_state)
+
+    batched_step()
+    torch.cuda.synchronize()
+    s = torch.cuda.Stream()
+    s.wait_stream(torch.cuda.current_stream())
+    g = torch.cuda.CUDAGraph()
+    with torch.cuda.stream(s):
+        batched_step()
+    torch.cuda.current_stream().wait_stream(s)
+    with torch.cuda.graph(g):
+        batched_step()
+    out = {"workload": "batched-16: " + ", ".join(f"{b.n}x{b.geom.n_sensors}x{b.geom.n_samples}x{b.F}"
+                                                   for b in scenes),
+           "contributions_per_step": C, "tiles": list(tiles) if tiles else None, "steps": args.steps_batched}
+    for mode, fn in (("graph_persistent", g.replay), ("per_scene", per_scene_step)):
+        fn()
+        torch.cuda.synchronize()
+        ms = 0.0
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        for _ in range(args.steps_batched):
+            flush.zero_()
+            e0.record()
+            fn()
+            e1.record()
+            e1.synchronize()
+            ms += e0.elapsed_time(e1)
+        out[f"{mode}_ms_per_step"] = ms / args.steps_batched
+        out[f"{mode}_contrib_per_s"] = C * args.steps_batched / (ms * 1e-3)
+    pa.device_error()
+    out["speedup_persistent_vs_per_scene"] = out["per_scene_ms_per_step"] / out["graph_persistent_ms_per_step"]
     return out
 
 

@@ -117,6 +117,20 @@ typedef struct pa_grads {
     float *sigma;
 } pa_grads;
 
+/* One scene of a batched call: its own sensor array, acquisition scalars,
+ * per-frame ball states and outputs.  Scenes may differ in every size. */
+typedef struct pa_scene {
+    pa_geom geom;
+    pa_balls balls;          /* device [n_frames][5][stride] */
+    int32_t n_frames;
+    float *traces;           /* pa_forward_batched output, device [n_frames][S][T], 16-byte aligned */
+    const float *trace_grad; /* pa_adjoint_batched input, device [n_frames][S][T] */
+    float *grad_state;       /* pa_adjoint_batched output, device [n_frames][5][stride] */
+} pa_scene;
+
+/* Most scenes one batched call takes. */
+#define PA_MAX_SCENES 64
+
 /* Human-readable name of a status code (static storage). */
 PA_API const char *pa_status_string(int32_t status);
 
@@ -185,6 +199,29 @@ PA_API int32_t pa_forward_plan_info(const pa_geom *geom, const pa_balls *balls, 
 PA_API int32_t pa_adjoint(const pa_geom *geom, const pa_balls *balls, const pa_canon *canon,
                    const float *t_frames, int32_t n_frames, const float *trace_grad,
                    const float *frame_scale, pa_grads *grads, uint32_t flags, void *stream);
+
+/* Scratch bytes a batched call needs (its work-queue counter). */
+PA_API size_t pa_batched_workspace_size(void);
+
+/* Forward projection of several independent scenes of uneven ball, sensor,
+ * sample and frame counts in one persistent launch (the batching of Sec. 1:
+ * one cloud per scene for all its frames; several scenes per launch).  The
+ * work items (scene, frame, sensor tile, sample tile) are taken from a
+ * counter in the workspace, heaviest scenes first, by one CTA per SM.
+ * Each scene's traces equal pa_forward's (same tiles, no ball splits).
+ * scenes: host array of n_scenes (<= PA_MAX_SCENES); tiles: as for
+ * pa_forward_ex (ball splits ignored) or NULL; workspace: device, at least
+ * pa_batched_workspace_size() bytes, 16-byte aligned.  Only the Gaussian
+ * profile; flags: PA_ACCUMULATE. */
+PA_API int32_t pa_forward_batched(const pa_scene *scenes, int32_t n_scenes, uint32_t flags, const int32_t *tiles,
+                                  void *workspace, size_t workspace_bytes, void *stream);
+
+/* Static-mode adjoint of several scenes in one persistent launch: warps take
+ * chunks of (scene, frame, ball) items from a counter in the workspace,
+ * scenes with the most sensors first.  Each scene's grad_state equals
+ * pa_adjoint's static mode.  flags: PA_ACCUMULATE. */
+PA_API int32_t pa_adjoint_batched(const pa_scene *scenes, int32_t n_scenes, uint32_t flags, void *workspace,
+                                  size_t workspace_bytes, void *stream);
 
 /* Scratch bytes pa_residual_loss needs. */
 PA_API size_t pa_loss_workspace_size(int64_t per_frame, int32_t n_frames);

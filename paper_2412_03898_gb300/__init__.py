@@ -24,7 +24,7 @@ from ._lib import PAError
 __all__ = [
     "PAError", "Geometry", "round4", "pad_last", "deform_balls", "forward", "adjoint", "residual_loss", "sumsq",
     "count_contributions", "adam_step", "device_error", "forward_plan", "forward_workspace_size",
-    "PAProject", "PAProject4D", "PALoss",
+    "PAProject", "PAProject4D", "PALoss", "Scene", "forward_batched", "adjoint_batched",
 ]
 
 
@@ -281,6 +281,66 @@ def adam_step(x: torch.Tensor, g: torch.Tensor, m: torch.Tensor, v: torch.Tensor
         _check(t, nm)
     _lib.check(_LIB.pa_adam_step(x.data_ptr(), g.data_ptr(), m.data_ptr(), v.data_ptr(), x.numel(), float(lr),
                                  float(beta1), float(beta2), float(eps), int(step), _stream()), "pa_adam_step")
+
+
+class Scene:
+    """One scene of a batched call (pa_scene): geometry, per-frame states
+    [F, 5, stride] and the buffers the batched calls read or write."""
+
+    def __init__(self, geom: Geometry, state: torch.Tensor, n: Optional[int] = None,
+                 traces: Optional[torch.Tensor] = None, trace_grad: Optional[torch.Tensor] = None,
+                 grad_state: Optional[torch.Tensor] = None):
+        self.geom = geom
+        self.state, self._balls, self.n = _balls_struct(state, n)
+        self.F = int(self.state.shape[0])
+        self.traces = traces
+        self.trace_grad = trace_grad
+        self.grad_state = grad_state
+
+    def struct(self) -> _lib.pa_scene:
+        return _lib.pa_scene(self.geom.struct(), self._balls, self.F, _ptr(self.traces), _ptr(self.trace_grad),
+                             _ptr(self.grad_state))
+
+
+def _scene_array(scenes):
+    if len(scenes) > _lib.PA_MAX_SCENES:
+        raise ValueError(f"at most {_lib.PA_MAX_SCENES} scenes per batched call")
+    return (_lib.pa_scene * max(len(scenes), 1))(*[sc.struct() for sc in scenes])
+
+
+def forward_batched(scenes, tiles: Optional[Sequence[int]] = None, accumulate: bool = False,
+                    workspace: Optional[torch.Tensor] = None):
+    """Forward projection of several scenes in one persistent launch; fills
+    (allocating if needed) each scene's traces [F, S, T]."""
+    for sc in scenes:
+        if sc.traces is None:
+            sc.traces = torch.empty(sc.F, sc.geom.n_sensors, sc.geom.n_samples, dtype=torch.float32,
+                                    device=sc.state.device)
+        _check(sc.traces, "traces")
+    arr = _scene_array(scenes)
+    dev = scenes[0].state.device if scenes else torch.device("cuda")
+    if workspace is None:
+        workspace = torch.empty(int(_LIB.pa_batched_workspace_size()), dtype=torch.uint8, device=dev)
+    _lib.check(_LIB.pa_forward_batched(arr, len(scenes), _lib.PA_ACCUMULATE if accumulate else 0, _tiles(tiles),
+                                       workspace.data_ptr(), workspace.numel(), _stream()), "pa_forward_batched")
+    return [sc.traces for sc in scenes]
+
+
+def adjoint_batched(scenes, accumulate: bool = False, workspace: Optional[torch.Tensor] = None):
+    """Static-mode adjoint of several scenes in one persistent launch; reads
+    each scene's trace_grad and fills its grad_state [F, 5, stride]."""
+    for sc in scenes:
+        _check(sc.trace_grad, "trace_grad")
+        if sc.grad_state is None:
+            sc.grad_state = torch.empty_like(sc.state)
+        _check(sc.grad_state, "grad_state")
+    arr = _scene_array(scenes)
+    dev = scenes[0].state.device if scenes else torch.device("cuda")
+    if workspace is None:
+        workspace = torch.empty(int(_LIB.pa_batched_workspace_size()), dtype=torch.uint8, device=dev)
+    _lib.check(_LIB.pa_adjoint_batched(arr, len(scenes), _lib.PA_ACCUMULATE if accumulate else 0,
+                                       workspace.data_ptr(), workspace.numel(), _stream()), "pa_adjoint_batched")
+    return [sc.grad_state for sc in scenes]
 
 
 # ---------------------------------------------------------------------------

@@ -44,6 +44,14 @@ class pa_grads(ctypes.Structure):
                 ("sigma", ctypes.c_void_p)]
 
 
+class pa_scene(ctypes.Structure):
+    _fields_ = [("geom", pa_geom), ("balls", pa_balls), ("n_frames", ctypes.c_int32), ("traces", ctypes.c_void_p),
+                ("trace_grad", ctypes.c_void_p), ("grad_state", ctypes.c_void_p)]
+
+
+PA_MAX_SCENES = 64
+
+
 class PAError(RuntimeError):
     def __init__(self, status: int, where: str):
         self.status = status
@@ -77,6 +85,9 @@ def load() -> ctypes.CDLL:
         "pa_forward_ex": (i32, [G, B, i32, P, u32, I32P, P, sz, P]),
         "pa_forward_plan_info": (i32, [G, B, i32, I32P, I32P]),
         "pa_adjoint": (i32, [G, B, C, P, i32, P, P, GR, u32, P]),
+        "pa_batched_workspace_size": (sz, []),
+        "pa_forward_batched": (i32, [ctypes.POINTER(pa_scene), i32, u32, I32P, P, sz, P]),
+        "pa_adjoint_batched": (i32, [ctypes.POINTER(pa_scene), i32, u32, P, sz, P]),
         "pa_loss_workspace_size": (sz, [i64, i32]),
         "pa_residual_loss": (i32, [P, P, i64, i32, P, P, P, P, sz, P]),
         "pa_residual_loss_noalloc": (i32, [P, P, i64, i32, P, P, P, P]),
@@ -108,4 +119,5 @@ def exported_symbols() -> list[str]:
     """Names of the C-ABI entry points declared in this module."""
     return ["pa_status_string", "pa_version", "pa_device_error", "pa_deform_balls", "pa_forward_workspace_size",
             "pa_forward_workspace_size_ex", "pa_forward", "pa_forward_ex", "pa_forward_plan_info", "pa_adjoint",
+            "pa_batched_workspace_size", "pa_forward_batched", "pa_adjoint_batched",
             "pa_loss_workspace_size", "pa_residual_loss", "pa_residual_loss_noalloc", "pa_sumsq", "pa_count_contributions", "pa_adam_step"]

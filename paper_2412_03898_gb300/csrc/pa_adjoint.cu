@@ -42,21 +42,22 @@ constexpr int kAdjGroup = 4;
 
 // dL/d(x, y, z, a, p) of one ball at frame f, summed over all sensors and
 // samples.  Returns the totals (identical in every lane).
-__device__ __forceinline__ void ball_frame_grad(const AdjArgs &A, const float *ssens, float4 *rec, int lane,
-                                                int f, float bx, float by, float bz, float a, float p,
-                                                float out[5], bool &dom) {
+// Sensor coordinates are read from sens[c * sstr + s] (shared memory, or the
+// global sensor array of a batched scene).
+__device__ __forceinline__ void ball_frame_grad(const Acq &q, const float *gframe, const float *sens, int sstr,
+                                                float4 *rec, int lane, float bx, float by, float bz, float a,
+                                                float p, float out[5], bool &dom) {
   constexpr int G = kAdjGroup;
-  const int S = A.q.S, T = A.q.T;
+  const int S = q.S, T = q.T;
   float gx = 0.f, gy = 0.f, gz = 0.f, ga = 0.f, gp = 0.f;
-  const float *gframe = A.g + (long long)f * S * T;
   if (a > 0.f && p != 0.f) {
     for (int s0 = 0; s0 < S; s0 += 32) {
       const int s = s0 + lane;
       int W = 0;
       float4 r0 = make_float4(0.f, 0.f, 0.f, 0.f), r1 = r0, r2 = r0;
       if (s < S) {
-        const float sx = ssens[s], sy = ssens[S + s], sz = ssens[2 * S + s];
-        const PairWin w = pair_window<false>(A.q, bx, by, bz, a, p, sx, sy, sz, 0, T - 1);
+        const float sx = sens[s], sy = sens[sstr + s], sz = sens[2 * sstr + s];
+        const PairWin w = pair_window<false>(q, bx, by, bz, a, p, sx, sy, sz, 0, T - 1);
         dom |= w.domain_err;
         W = w.W;
         if (W > 0) {
@@ -178,7 +179,8 @@ __global__ void __launch_bounds__(32 * kAdjWarps) k_adjoint_static(const AdjArgs
 #pragma unroll
     for (int c = 0; c < 5; ++c) v[c] = __shfl_sync(FULL, mine, c);
     float g[5];
-    ball_frame_grad(A, ssens, rec, lane, f, v[0], v[1], v[2], v[3], v[4], g, dom);
+    ball_frame_grad(A.q, A.g + (long long)f * A.q.S * A.q.T, ssens, A.q.S, rec, lane, v[0], v[1], v[2], v[3], v[4],
+                    g, dom);
     const float sc = A.frame_scale ? __ldg(A.frame_scale + f) : 1.f;
     if (lane < 5) {
       float gv = g[0];
@@ -242,8 +244,9 @@ __global__ void __launch_bounds__(32 * kAdjWarps) k_adjoint_4d(const AdjArgs A) 
         H[c] = warp_sum(h);
       }
       float g[5];
-      ball_frame_grad(A, ssens, rec, lane, f, q0[0] * (1.f + H[0]), q0[1] * (1.f + H[1]), q0[2] * (1.f + H[2]),
-                      q0[3] * (1.f + H[3]), q0[4] * (1.f + H[4]), g, dom);
+      ball_frame_grad(A.q, A.g + (long long)f * A.q.S * A.q.T, ssens, A.q.S, rec, lane, q0[0] * (1.f + H[0]),
+                      q0[1] * (1.f + H[1]), q0[2] * (1.f + H[2]), q0[3] * (1.f + H[3]), q0[4] * (1.f + H[4]), g,
+                      dom);
       const float sc = A.frame_scale ? __ldg(A.frame_scale + f) : 1.f;
 #pragma unroll
       for (int c = 0; c < 5; ++c) {
@@ -284,6 +287,49 @@ __global__ void __launch_bounds__(32 * kAdjWarps) k_adjoint_4d(const AdjArgs A) 
   if (dom) set_error(A.err, PA_ERR_DOMAIN);
 }
 
+// Batched static mode: persistent warps take chunks of (scene, frame, ball)
+// items from a global counter; scenes are ordered heaviest first by the host.
+constexpr int kAdjChunk = 8;
+
+__global__ void __launch_bounds__(32 * kAdjWarps) k_adjoint_batched(const BatchAdjArgs A) {
+  __shared__ __align__(16) float4 recs[kAdjWarps * 96];
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  float4 *rec = recs + warp * 96;
+  bool dom = false;
+  while (true) {
+    unsigned long long base = 0;
+    if (lane == 0) base = atomicAdd(A.counter, (unsigned long long)kAdjChunk);
+    base = __shfl_sync(FULL, base, 0);
+    if ((long long)base >= A.total_items) break;
+    const long long end = min((long long)base + kAdjChunk, A.total_items);
+    for (long long item = (long long)base; item < end; ++item) {
+      int sc = 0;
+      while (sc + 1 < A.n_scenes && item >= A.sc[sc + 1].item_begin) ++sc;
+      const SceneAdj &d = A.sc[sc];
+      const long long local = item - d.item_begin;
+      const int f = (int)(local / d.n);
+      const long long b = local - (long long)f * d.n;
+      const float *st = d.state + (long long)f * 5 * d.stride;
+      const float mine = lane < 5 ? st[lane * d.stride + b] : 0.f;
+      float v[5];
+#pragma unroll
+      for (int c = 0; c < 5; ++c) v[c] = __shfl_sync(FULL, mine, c);
+      float g[5];
+      ball_frame_grad(d.q, d.g + (long long)f * d.q.S * d.q.T, d.q.sensors, d.q.sstride, rec, lane, v[0], v[1], v[2],
+                      v[3], v[4], g, dom);
+      if (lane < 5) {
+        float gv = g[0];
+#pragma unroll
+        for (int c = 1; c < 5; ++c)
+          if (lane == c) gv = g[c];
+        float *dst = d.g_state + (long long)f * 5 * d.stride + lane * d.stride + b;
+        *dst = (A.flags & PA_ACCUMULATE) ? *dst + gv : gv;
+      }
+    }
+  }
+  if (dom) set_error(A.err, PA_ERR_DOMAIN);
+}
+
 size_t adj_static_smem(int S) { return sizeof(float4) * kAdjWarps * 96 + sizeof(float) * 3 * (size_t)S; }
 size_t adj_4d_smem(int S, int nb) {
   return adj_static_smem(S) + sizeof(float) * (size_t)kAdjWarps * 6 * 5 * nb;
@@ -308,6 +354,20 @@ cudaError_t launch_gridstride(K kern, const AdjArgs &a, size_t smem, int sms, cu
 cudaError_t launch_adjoint_static(const AdjArgs &a, int sms, cudaStream_t st) {
   if (a.n_items == 0) return cudaSuccess;
   return launch_gridstride(k_adjoint_static, a, adj_static_smem(a.q.S), sms, st);
+}
+
+cudaError_t launch_adjoint_batched(const BatchAdjArgs &a, int sms, cudaStream_t st) {
+  if (a.total_items == 0) return cudaSuccess;
+  int occ = 0;
+  cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_adjoint_batched, 32 * kAdjWarps, 0);
+  if (e != cudaSuccess) return e;
+  if (occ < 1) return cudaErrorInvalidConfiguration;
+  e = cudaMemsetAsync(a.counter, 0, sizeof(unsigned long long), st);
+  if (e != cudaSuccess) return e;
+  const long long need = (a.total_items + kAdjChunk - 1) / kAdjChunk;
+  const long long grid = std::max(1LL, std::min((need + kAdjWarps - 1) / kAdjWarps, (long long)sms * occ));
+  k_adjoint_batched<<<(unsigned)grid, 32 * kAdjWarps, 0, st>>>(a);
+  return cudaGetLastError();
 }
 
 cudaError_t launch_adjoint_4d(const AdjArgs &a, int sms, cudaStream_t st) {

@@ -1,5 +1,6 @@
 // C ABI of the library (declared in include/pa.h): host-side validation,
 // tile plans, the per-device error word, and kernel launches.
+#include <algorithm>
 #include <cmath>
 #include <cstdint>
 #include <cstring>
@@ -290,6 +291,129 @@ int32_t pa_adjoint(const pa_geom *geom, const pa_balls *balls, const pa_canon *c
   const size_t smem = sizeof(float4) * 8 * 96 + sizeof(float) * 3 * (size_t)geom->n_sensors;
   if ((long long)smem > d->max_smem) return PA_ERR_INVALID_ARG;
   return cuda_status(pa::launch_adjoint_static(a, d->sms, st));
+}
+
+size_t pa_batched_workspace_size(void) { return 256; }
+
+int32_t pa_forward_batched(const pa_scene *scenes, int32_t n_scenes, uint32_t flags, const int32_t *tiles,
+                           void *workspace, size_t workspace_bytes, void *stream) {
+  if (n_scenes < 0 || n_scenes > PA_MAX_SCENES || (n_scenes > 0 && scenes == nullptr)) return PA_ERR_INVALID_ARG;
+  if ((flags & ~PA_ACCUMULATE) != 0) return PA_ERR_INVALID_ARG;
+  if (tiles && (tiles[0] < 0 || tiles[0] > 16 || tiles[1] < 0 || (tiles[1] & 3) != 0 || tiles[2] < 0 ||
+                (tiles[2] & 3) != 0 || tiles[4] < 0 || tiles[4] > 8))
+    return PA_ERR_INVALID_ARG;
+  if (workspace == nullptr || workspace_bytes < pa_batched_workspace_size() || !aligned(workspace, 16))
+    return PA_ERR_WORKSPACE;
+  const DevInfo *d = dev_info();
+  if (!d) return PA_ERR_CUDA;
+  cudaStream_t st = static_cast<cudaStream_t>(stream);
+  int maxT = 4;
+  for (int i = 0; i < n_scenes; ++i) {
+    const pa_scene &sc = scenes[i];
+    int rc = check_geom(&sc.geom);
+    if (rc) return rc;
+    if ((rc = check_balls(&sc.balls))) return rc;
+    if (sc.n_frames < 0) return PA_ERR_INVALID_ARG;
+    if (sc.n_frames > 0 && (sc.traces == nullptr || !aligned(sc.traces, 16))) return PA_ERR_INVALID_ARG;
+    maxT = std::max(maxT, sc.geom.n_samples);
+  }
+  const int s_tile = tiles && tiles[0] > 0 ? tiles[0] : 16;
+  int t_tile = tiles && tiles[1] > 0 ? tiles[1] : 2048;
+  t_tile = std::min(std::min(t_tile, maxT), 16384);
+  const int nb_tile = tiles && tiles[2] > 0 ? tiles[2] : 256;
+  const int group = tiles && tiles[4] == 4 ? 4 : 8;
+  const size_t smem = pa::forward_smem_bytes(s_tile, t_tile, nb_tile);
+  if ((long long)smem > d->max_smem) return PA_ERR_INVALID_ARG;
+  // scenes with balls, heaviest items (most balls) first
+  int order[PA_MAX_SCENES];
+  int m = 0;
+  for (int i = 0; i < n_scenes; ++i) {
+    const pa_scene &sc = scenes[i];
+    if (sc.n_frames == 0) continue;
+    if (sc.balls.n == 0) {
+      if (!(flags & PA_ACCUMULATE)) {
+        cudaError_t e = cudaMemsetAsync(
+            sc.traces, 0, sizeof(float) * (size_t)sc.n_frames * sc.geom.n_sensors * sc.geom.n_samples, st);
+        if (e != cudaSuccess) return PA_ERR_CUDA;
+      }
+      continue;
+    }
+    order[m++] = i;
+  }
+  std::sort(order, order + m, [&](int x, int y) { return scenes[x].balls.n > scenes[y].balls.n; });
+  pa::BatchFwdArgs a;
+  std::memset(&a, 0, sizeof(a));
+  a.n_scenes = m;
+  a.s_tile = s_tile;
+  a.t_tile = t_tile;
+  a.nb_tile = nb_tile;
+  a.counter = static_cast<unsigned long long *>(workspace);
+  a.flags = flags;
+  a.err = d->err;
+  long long items = 0;
+  for (int j = 0; j < m; ++j) {
+    const pa_scene &sc = scenes[order[j]];
+    pa::SceneFwd &o = a.sc[j];
+    o.q = make_acq(&sc.geom);
+    o.state = sc.balls.state;
+    o.n = sc.balls.n;
+    o.stride = sc.balls.stride;
+    o.out = sc.traces;
+    o.n_stiles = (sc.geom.n_sensors + s_tile - 1) / s_tile;
+    o.n_ttiles = (sc.geom.n_samples + t_tile - 1) / t_tile;
+    o.item_begin = items;
+    items += (long long)sc.n_frames * o.n_stiles * o.n_ttiles;
+  }
+  a.total_items = items;
+  if (items == 0) return PA_OK;
+  return cuda_status(pa::launch_forward_batched(a, group, smem, d->sms, st));
+}
+
+int32_t pa_adjoint_batched(const pa_scene *scenes, int32_t n_scenes, uint32_t flags, void *workspace,
+                           size_t workspace_bytes, void *stream) {
+  if (n_scenes < 0 || n_scenes > PA_MAX_SCENES || (n_scenes > 0 && scenes == nullptr)) return PA_ERR_INVALID_ARG;
+  if ((flags & ~PA_ACCUMULATE) != 0) return PA_ERR_INVALID_ARG;
+  if (workspace == nullptr || workspace_bytes < pa_batched_workspace_size() || !aligned(workspace, 16))
+    return PA_ERR_WORKSPACE;
+  const DevInfo *d = dev_info();
+  if (!d) return PA_ERR_CUDA;
+  int order[PA_MAX_SCENES];
+  int m = 0;
+  for (int i = 0; i < n_scenes; ++i) {
+    const pa_scene &sc = scenes[i];
+    int rc = check_geom(&sc.geom);
+    if (rc) return rc;
+    if ((rc = check_balls(&sc.balls))) return rc;
+    if (sc.n_frames < 0) return PA_ERR_INVALID_ARG;
+    if (sc.n_frames == 0 || sc.balls.n == 0) continue;
+    if (sc.trace_grad == nullptr || sc.grad_state == nullptr) return PA_ERR_INVALID_ARG;
+    order[m++] = i;
+  }
+  std::sort(order, order + m,
+            [&](int x, int y) { return scenes[x].geom.n_sensors > scenes[y].geom.n_sensors; });
+  pa::BatchAdjArgs a;
+  std::memset(&a, 0, sizeof(a));
+  a.n_scenes = m;
+  a.counter = static_cast<unsigned long long *>(workspace);
+  a.flags = flags;
+  a.err = d->err;
+  long long items = 0;
+  for (int j = 0; j < m; ++j) {
+    const pa_scene &sc = scenes[order[j]];
+    pa::SceneAdj &o = a.sc[j];
+    o.q = make_acq(&sc.geom);
+    o.state = sc.balls.state;
+    o.n = sc.balls.n;
+    o.stride = sc.balls.stride;
+    o.F = sc.n_frames;
+    o.g = sc.trace_grad;
+    o.g_state = sc.grad_state;
+    o.item_begin = items;
+    items += (long long)sc.n_frames * sc.balls.n;
+  }
+  a.total_items = items;
+  if (items == 0) return PA_OK;
+  return cuda_status(pa::launch_adjoint_batched(a, d->sms, static_cast<cudaStream_t>(stream)));
 }
 
 size_t pa_loss_workspace_size(int64_t per_frame, int32_t n_frames) {

@@ -32,43 +32,45 @@ namespace {
 
 constexpr int kMaxThreads = 512;  // at most 16 sensors (warps) per CTA
 
+// Shared-memory layout of a forward CTA.
+struct FwdSmem {
+  uint64_t *bars;  // 2 mbarriers (TMA stages)
+  float *sball;    // [2][5][nb_tile] ball tiles
+  float4 *srec;    // [s_tile][32] pair records
+  float *str;      // [s_tile][t_tile] trace tiles
+};
+
+__device__ __forceinline__ FwdSmem fwd_smem(unsigned char *raw, int s_tile, int nb_tile) {
+  FwdSmem m;
+  m.bars = reinterpret_cast<uint64_t *>(raw);
+  m.sball = reinterpret_cast<float *>(raw + 128);
+  m.srec = reinterpret_cast<float4 *>(m.sball + 2 * 5 * nb_tile);
+  m.str = reinterpret_cast<float *>(m.srec + s_tile * 32);
+  return m;
+}
+
+// One work item: frame state `state_f`, sensors [st*s_tile, +s_tile), samples
+// [k0, k0+klen), balls [b_begin, b_end).  Writes (or adds) the trace tile to
+// dst_f[s][k] (frame base of a [S][T] array).  `phase` holds the parity of
+// each TMA stage's next completion and is carried across items of a
+// persistent CTA.  Returns false after a bounded wait ran out.
 template <bool UNIFORM, int G>
-__global__ void __launch_bounds__(kMaxThreads, 1) k_forward(const FwdArgs A) {
-  extern __shared__ __align__(128) unsigned char smem_raw[];
-  uint64_t *bars = reinterpret_cast<uint64_t *>(smem_raw);
-  float *sball = reinterpret_cast<float *>(smem_raw + 128);
-  float4 *srec = reinterpret_cast<float4 *>(sball + 2 * 5 * A.nb_tile);
-  float *str = reinterpret_cast<float *>(srec + A.s_tile * 32);
-
+__device__ __forceinline__ bool forward_item(const Acq &q, const float *state_f, long long stride,
+                                             long long b_begin, long long b_end, int s_tile, int t_tile, int nbt,
+                                             int st, int k0, int klen, float *dst_f, bool acc, const FwdSmem &m,
+                                             unsigned &phase, unsigned *err) {
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
-  int item = blockIdx.x;
-  const int split = item % A.n_splits;
-  item /= A.n_splits;
-  const int tt = item % A.n_ttiles;
-  item /= A.n_ttiles;
-  const int st = item % A.n_stiles;
-  const int f = item / A.n_stiles;
+  const int T = q.T;
+  const int s = st * s_tile + warp;
+  const bool s_ok = s < q.S;
+  const int ntiles = b_end > b_begin ? (int)((b_end - b_begin + nbt - 1) / nbt) : 0;
+  float *sball = m.sball;
+  uint64_t *bars = m.bars;
 
-  const int T = A.q.T;
-  const int k0 = tt * A.t_tile;
-  const int klen = min(A.t_tile, T - k0);
-  const int s = st * A.s_tile + warp;
-  const bool s_ok = s < A.q.S;
-  const long long b_begin = (long long)split * A.balls_per_split;
-  const long long b_end = min(A.n, b_begin + A.balls_per_split);
-  const int ntiles = b_end > b_begin ? (int)((b_end - b_begin + A.nb_tile - 1) / A.nb_tile) : 0;
-  const float *state_f = A.state + (long long)f * 5 * A.stride;
-  const int nbt = A.nb_tile;
-
-  float4 *str4 = reinterpret_cast<float4 *>(str);
-  const int nz = A.s_tile * A.t_tile / 4;
+  __syncthreads();  // the previous item (if any) is done with the trace tiles
+  float4 *str4 = reinterpret_cast<float4 *>(m.str);
+  const int nz = s_tile * t_tile / 4;
   for (int i = tid; i < nz; i += blockDim.x) str4[i] = make_float4(0.f, 0.f, 0.f, 0.f);
-  if (tid == 0) {
-    mbar_init(&bars[0], 1);
-    mbar_init(&bars[1], 1);
-    fence_barrier_init();
-  }
-  __syncthreads();
 
   auto issue = [&](int t) {
     const int stage = t & 1;
@@ -78,29 +80,32 @@ __global__ void __launch_bounds__(kMaxThreads, 1) k_forward(const FwdArgs A) {
     mbar_arrive_expect_tx(&bars[stage], 5u * bytes);
 #pragma unroll
     for (int ch = 0; ch < 5; ++ch)
-      bulk_copy_g2s(sball + (stage * 5 + ch) * nbt, state_f + ch * A.stride + b0, bytes, &bars[stage]);
+      bulk_copy_g2s(sball + (stage * 5 + ch) * nbt, state_f + ch * stride + b0, bytes, &bars[stage]);
   };
   if (tid == 0) {
     fence_proxy_async();
     if (ntiles > 0) issue(0);
     if (ntiles > 1) issue(1);
   }
+  __syncthreads();  // trace tiles zeroed
 
   float sx = 0.f, sy = 0.f, sz = 0.f;
   if (s_ok) {
-    sx = A.q.sensors[s];
-    sy = A.q.sensors[A.q.sstride + s];
-    sz = A.q.sensors[2 * A.q.sstride + s];
+    sx = q.sensors[s];
+    sy = q.sensors[q.sstride + s];
+    sz = q.sensors[2 * q.sstride + s];
   }
-  float *mytr = str + warp * A.t_tile;
-  float4 *myrec = srec + warp * 32;
+  float *mytr = m.str + warp * t_tile;
+  float4 *myrec = m.srec + warp * 32;
   bool dom = false;
   // window bound in scaled units: |u| <= kappa K_S (Gaussian), |u| <= 1 (uniform)
-  const float umax2 = UNIFORM ? 1.f : (A.q.kappa * K_S) * (A.q.kappa * K_S);
+  const float umax2 = UNIFORM ? 1.f : (q.kappa * K_S) * (q.kappa * K_S);
 
   for (int t = 0; t < ntiles; ++t) {
     const int stage = t & 1;
-    const bool ok = mbar_wait_bounded(&bars[stage], (t >> 1) & 1);
+    const unsigned par = (phase >> stage) & 1u;
+    const bool ok = mbar_wait_bounded(&bars[stage], par);
+    phase ^= 1u << stage;
     const int cnt = (int)min((long long)nbt, b_end - (b_begin + (long long)t * nbt));
     if (ok && s_ok) {
       const float *bx = sball + stage * 5 * nbt;
@@ -111,9 +116,9 @@ __global__ void __launch_bounds__(kMaxThreads, 1) k_forward(const FwdArgs A) {
         if (bi < cnt) {
           const float dx = bx[bi] - sx, dy = bx[nbt + bi] - sy, dz = bx[2 * nbt + bi] - sz;
           const float a = bx[3 * nbt + bi];
-          const float h = (UNIFORM ? 1.f : A.q.kappa) * a;
-          const float rc = sqrtf(fmaf(dx, dx, fmaf(dy, dy, dz * dz))) - A.q.ct0h;
-          const float lo = (rc - h) * A.q.inv_delta, hi = (rc + h) * A.q.inv_delta;
+          const float h = (UNIFORM ? 1.f : q.kappa) * a;
+          const float rc = sqrtf(fmaf(dx, dx, fmaf(dy, dy, dz * dz))) - q.ct0h;
+          const float lo = (rc - h) * q.inv_delta, hi = (rc + h) * q.inv_delta;
           maybe = a > 0.f && bx[4 * nbt + bi] != 0.f && hi >= (float)(k0 - 2) && lo <= (float)(k0 + klen + 1);
         }
         if (__ballot_sync(FULL, maybe) == 0) continue;
@@ -121,7 +126,7 @@ __global__ void __launch_bounds__(kMaxThreads, 1) k_forward(const FwdArgs A) {
         w.W = 0;
         w.domain_err = false;
         if (bi < cnt)
-          w = pair_window<UNIFORM>(A.q, bx[bi], bx[nbt + bi], bx[2 * nbt + bi], bx[3 * nbt + bi],
+          w = pair_window<UNIFORM>(q, bx[bi], bx[nbt + bi], bx[2 * nbt + bi], bx[3 * nbt + bi],
                                    bx[4 * nbt + bi], sx, sy, sz, k0, k0 + klen - 1);
         dom |= w.domain_err;
         const bool valid = w.W > 0;
@@ -187,32 +192,28 @@ __global__ void __launch_bounds__(kMaxThreads, 1) k_forward(const FwdArgs A) {
           __syncwarp();
         }
       }
-    }
+        }
     const int abort = __syncthreads_or(!ok);
     if (abort) {
-      // A copy did not complete in time: record it, give the copies still in
-      // flight a bounded chance to land, and leave without writing output.
+      // A copy did not complete in time: record it and give the copy still in
+      // flight a bounded chance to land before the shared memory is reused.
       if (tid == 0) {
-        set_error(A.err, PA_ERR_TIMEOUT);
-        mbar_wait_bounded(&bars[t & 1], (t >> 1) & 1);
-        if (t + 1 < ntiles) mbar_wait_bounded(&bars[(t + 1) & 1], ((t + 1) >> 1) & 1);
+        set_error(err, PA_ERR_TIMEOUT);
+        mbar_wait_bounded(&bars[stage], par);
+        if (t + 1 < ntiles) mbar_wait_bounded(&bars[(t + 1) & 1], (phase >> ((t + 1) & 1)) & 1u);
       }
       __syncthreads();
-      return;
+      return false;
     }
     if (tid == 0 && t + 2 < ntiles) {
       fence_proxy_async();
       issue(t + 2);
     }
   }
-  if (dom) set_error(A.err, PA_ERR_DOMAIN);
+  if (dom) set_error(err, PA_ERR_DOMAIN);
 
   if (s_ok) {
-    const long long base = ((long long)f * A.q.S + s) * T + k0;
-    const bool single = A.n_splits == 1;
-    float *dst = single ? A.out + base : A.partial + (long long)split * A.F * A.q.S * T + base;
-    const bool acc = single && (A.flags & PA_ACCUMULATE);
-    float4 *d4 = reinterpret_cast<float4 *>(dst);
+    float4 *d4 = reinterpret_cast<float4 *>(dst_f + (long long)s * T + k0);
     const float4 *s4 = reinterpret_cast<const float4 *>(mytr);
     for (int i = lane; i < klen / 4; i += 32) {
       float4 v = s4[i];
@@ -225,6 +226,75 @@ __global__ void __launch_bounds__(kMaxThreads, 1) k_forward(const FwdArgs A) {
       }
       d4[i] = v;
     }
+  }
+  return true;
+}
+
+__device__ __forceinline__ void init_bars(uint64_t *bars) {
+  if (threadIdx.x == 0) {
+    mbar_init(&bars[0], 1);
+    mbar_init(&bars[1], 1);
+    fence_barrier_init();
+  }
+  __syncthreads();
+}
+
+// One CTA per (frame, sensor tile, sample tile, ball split).
+template <bool UNIFORM, int G>
+__global__ void __launch_bounds__(kMaxThreads, 1) k_forward(const FwdArgs A) {
+  extern __shared__ __align__(128) unsigned char smem_raw[];
+  const FwdSmem m = fwd_smem(smem_raw, A.s_tile, A.nb_tile);
+  init_bars(m.bars);
+  int item = blockIdx.x;
+  const int split = item % A.n_splits;
+  item /= A.n_splits;
+  const int tt = item % A.n_ttiles;
+  item /= A.n_ttiles;
+  const int st = item % A.n_stiles;
+  const int f = item / A.n_stiles;
+  const int T = A.q.T;
+  const int k0 = tt * A.t_tile;
+  const int klen = min(A.t_tile, T - k0);
+  const long long b_begin = (long long)split * A.balls_per_split;
+  const long long b_end = min(A.n, b_begin + A.balls_per_split);
+  const bool single = A.n_splits == 1;
+  float *dst_f = single ? A.out + (long long)f * A.q.S * T
+                        : A.partial + ((long long)split * A.F + f) * A.q.S * T;
+  unsigned phase = 0;
+  forward_item<UNIFORM, G>(A.q, A.state + (long long)f * 5 * A.stride, A.stride, b_begin, b_end, A.s_tile, A.t_tile,
+                           A.nb_tile, st, k0, klen, dst_f, single && (A.flags & PA_ACCUMULATE), m, phase, A.err);
+}
+
+// Persistent CTAs over the work items of several scenes: an item is
+// (scene, frame, sensor tile, sample tile), taken from a global counter in
+// the order of the scene table (the host orders scenes by item cost,
+// heaviest first).
+template <int G>
+__global__ void __launch_bounds__(kMaxThreads, 1) k_forward_batched(const BatchFwdArgs A) {
+  extern __shared__ __align__(128) unsigned char smem_raw[];
+  const FwdSmem m = fwd_smem(smem_raw, A.s_tile, A.nb_tile);
+  __shared__ long long s_item;
+  init_bars(m.bars);
+  unsigned phase = 0;
+  while (true) {
+    if (threadIdx.x == 0) s_item = (long long)atomicAdd(A.counter, 1ull);
+    __syncthreads();
+    const long long item = s_item;
+    if (item >= A.total_items) break;
+    int sc = 0;
+    while (sc + 1 < A.n_scenes && item >= A.sc[sc + 1].item_begin) ++sc;
+    const SceneFwd &d = A.sc[sc];
+    long long local = item - d.item_begin;
+    const int tt = (int)(local % d.n_ttiles);
+    local /= d.n_ttiles;
+    const int st = (int)(local % d.n_stiles);
+    const int f = (int)(local / d.n_stiles);
+    const int k0 = tt * A.t_tile;
+    const int klen = min(A.t_tile, d.q.T - k0);
+    const bool ok = forward_item<false, G>(d.q, d.state + (long long)f * 5 * d.stride, d.stride, 0, d.n, A.s_tile,
+                                           A.t_tile, A.nb_tile, st, k0, klen, d.out + (long long)f * d.q.S * d.q.T,
+                                           (A.flags & PA_ACCUMULATE) != 0, m, phase, A.err);
+    if (!ok) break;
   }
 }
 
@@ -351,6 +421,21 @@ cudaError_t launch_forward(const FwdArgs &a, const FwdPlan &p, bool uniform, cud
   k_reduce_splits<<<(unsigned)std::max(1LL, blocks), 256, 0, st>>>(
       reinterpret_cast<const float4 *>(a.partial), reinterpret_cast<float4 *>(a.out), n4, p.n_splits,
       (a.flags & PA_ACCUMULATE) != 0);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_forward_batched(const BatchFwdArgs &a, int group, size_t smem, int sms, cudaStream_t st) {
+  auto fn = group == 4 ? k_forward_batched<4> : k_forward_batched<8>;
+  cudaError_t e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  if (e != cudaSuccess) return e;
+  int occ = 0;
+  e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, fn, 32 * a.s_tile, smem);
+  if (e != cudaSuccess) return e;
+  if (occ < 1) return cudaErrorInvalidConfiguration;
+  e = cudaMemsetAsync(a.counter, 0, sizeof(unsigned long long), st);
+  if (e != cudaSuccess) return e;
+  const long long grid = std::max(1LL, std::min(a.total_items, (long long)sms * occ));
+  fn<<<(unsigned)grid, 32 * a.s_tile, smem, st>>>(a);
   return cudaGetLastError();
 }
 

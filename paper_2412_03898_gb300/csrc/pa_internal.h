@@ -35,6 +35,47 @@ struct FwdArgs {
   unsigned *err;
 };
 
+// Batched (several scenes, one persistent launch).
+constexpr int kMaxScenes = 64;
+
+struct SceneFwd {
+  Acq q;
+  const float *state;
+  long long n, stride;
+  float *out;
+  int n_stiles, n_ttiles;
+  long long item_begin;  // first work item of this scene
+};
+
+struct BatchFwdArgs {
+  int n_scenes;
+  int s_tile, t_tile, nb_tile;
+  long long total_items;
+  unsigned long long *counter;  // work-queue counter, zero at launch
+  unsigned flags;
+  unsigned *err;
+  SceneFwd sc[kMaxScenes];
+};
+
+struct SceneAdj {
+  Acq q;
+  const float *state;
+  long long n, stride;
+  int F;
+  const float *g;
+  float *g_state;
+  long long item_begin;  // first (frame, ball) item of this scene
+};
+
+struct BatchAdjArgs {
+  int n_scenes;
+  long long total_items;
+  unsigned long long *counter;
+  unsigned flags;
+  unsigned *err;
+  SceneAdj sc[kMaxScenes];
+};
+
 struct AdjArgs {
   Acq q;
   // static mode
@@ -61,6 +102,8 @@ size_t forward_smem_bytes(int s_tile, int t_tile, int nb_tile);
 int forward_blocks_per_sm(const FwdPlan &p, bool uniform);
 
 cudaError_t launch_forward(const FwdArgs &a, const FwdPlan &p, bool uniform, cudaStream_t st);
+cudaError_t launch_forward_batched(const BatchFwdArgs &a, int group, size_t smem, int sms, cudaStream_t st);
+cudaError_t launch_adjoint_batched(const BatchAdjArgs &a, int sms, cudaStream_t st);
 cudaError_t launch_count(const Acq &q, const float *state, long long n, long long stride, int F,
                          unsigned long long *out, cudaStream_t st);
 cudaError_t launch_adjoint_static(const AdjArgs &a, int sms, cudaStream_t st);
