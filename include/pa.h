@@ -277,6 +277,18 @@ PA_API int32_t pa_count_contributions(const pa_geom *geom, const pa_balls *balls
 PA_API int32_t pa_adam_step(float *x, const float *g, float *m, float *v, int64_t n, double lr, double beta1,
                             double beta2, double eps, int32_t step, void *stream);
 
+/* Adam with the step number read from device memory, so that a whole IR
+ * iteration can be replayed from one CUDA graph: t = *step (>= 1), learning
+ * rate lr0 * gamma^floor((t-1)/step_size) (the step decay of Sec. 3.2:
+ * step_size 160, drop rate 0.1), bias corrections 1 - beta^t.  Otherwise as
+ * pa_adam_step.  step: device int32. */
+PA_API int32_t pa_adam_step_scheduled(float *x, const float *g, float *m, float *v, int64_t n, double lr0,
+                                      double beta1, double beta2, double eps, int32_t step_size, double gamma,
+                                      const int32_t *step, void *stream);
+
+/* Adds 1 to the device int32 *step (one-thread kernel, stream ordered). */
+PA_API int32_t pa_step_increment(int32_t *step, void *stream);
+
 #ifdef __cplusplus
 }
 #endif

@@ -24,7 +24,7 @@ from ._lib import PAError
 __all__ = [
     "PAError", "Geometry", "round4", "pad_last", "deform_balls", "forward", "adjoint", "residual_loss", "sumsq",
     "count_contributions", "adam_step", "device_error", "forward_plan", "forward_workspace_size",
-    "PAProject", "PAProject4D", "PALoss", "Scene", "forward_batched", "adjoint_batched",
+    "PAProject", "PAProject4D", "PALoss", "Scene", "forward_batched", "adjoint_batched", "adam_step_scheduled", "step_increment",
 ]
 
 
@@ -341,6 +341,24 @@ def adjoint_batched(scenes, accumulate: bool = False, workspace: Optional[torch.
     _lib.check(_LIB.pa_adjoint_batched(arr, len(scenes), _lib.PA_ACCUMULATE if accumulate else 0,
                                        workspace.data_ptr(), workspace.numel(), _stream()), "pa_adjoint_batched")
     return [sc.grad_state for sc in scenes]
+
+
+def adam_step_scheduled(x: torch.Tensor, g: torch.Tensor, m: torch.Tensor, v: torch.Tensor, lr0: float,
+                        step: torch.Tensor, step_size: int = 160, gamma: float = 0.1, beta1: float = 0.9,
+                        beta2: float = 0.999, eps: float = 1e-8) -> None:
+    """Adam whose step number t (and so the step-decayed learning rate and the
+    bias corrections) is read from the device int32 tensor `step`."""
+    for t, nm in ((x, "x"), (g, "g"), (m, "m"), (v, "v")):
+        _check(t, nm)
+    _check(step, "step", torch.int32)
+    _lib.check(_LIB.pa_adam_step_scheduled(x.data_ptr(), g.data_ptr(), m.data_ptr(), v.data_ptr(), x.numel(),
+                                           float(lr0), float(beta1), float(beta2), float(eps), int(step_size),
+                                           float(gamma), step.data_ptr(), _stream()), "pa_adam_step_scheduled")
+
+
+def step_increment(step: torch.Tensor) -> None:
+    _check(step, "step", torch.int32)
+    _lib.check(_LIB.pa_step_increment(step.data_ptr(), _stream()), "pa_step_increment")
 
 
 # ---------------------------------------------------------------------------

@@ -94,6 +94,9 @@ def load() -> ctypes.CDLL:
         "pa_sumsq": (i32, [P, i64, P, P, sz, P]),
         "pa_count_contributions": (i32, [G, B, i32, P, P]),
         "pa_adam_step": (i32, [P, P, P, P, i64, ctypes.c_double, ctypes.c_double, ctypes.c_double, ctypes.c_double, i32, P]),
+        "pa_adam_step_scheduled": (i32, [P, P, P, P, i64, ctypes.c_double, ctypes.c_double, ctypes.c_double,
+                                         ctypes.c_double, i32, ctypes.c_double, P, P]),
+        "pa_step_increment": (i32, [P, P]),
     }
     for name, (res, args) in sig.items():
         fn = getattr(lib, name)
@@ -120,4 +123,5 @@ def exported_symbols() -> list[str]:
     return ["pa_status_string", "pa_version", "pa_device_error", "pa_deform_balls", "pa_forward_workspace_size",
             "pa_forward_workspace_size_ex", "pa_forward", "pa_forward_ex", "pa_forward_plan_info", "pa_adjoint",
             "pa_batched_workspace_size", "pa_forward_batched", "pa_adjoint_batched",
-            "pa_loss_workspace_size", "pa_residual_loss", "pa_residual_loss_noalloc", "pa_sumsq", "pa_count_contributions", "pa_adam_step"]
+            "pa_loss_workspace_size", "pa_residual_loss", "pa_residual_loss_noalloc", "pa_sumsq", "pa_count_contributions", "pa_adam_step",
+            "pa_adam_step_scheduled", "pa_step_increment"]

@@ -19,7 +19,7 @@ from . import Geometry, forward, forward_batched, forward_plan, forward_workspac
 
 # (s_tile, t_tile, nb_tile, splits, group); splits 0 = the planner's choice
 DEFAULT_CANDIDATES = [
-    (16, 2048, 256, 0, 8), (16, 2048, 512, 0, 8), (16, 2048, 128, 0, 8), (8, 2048, 256, 0, 8),
+    (12, 4096, 512, 0, 8), (12, 4096, 256, 0, 8), (16, 2048, 256, 0, 8), (16, 2048, 512, 0, 8), (16, 2048, 128, 0, 8), (8, 2048, 256, 0, 8),
     (8, 4096, 512, 0, 8), (4, 4096, 256, 0, 8), (16, 2048, 256, 0, 4), (12, 2048, 256, 0, 8),
 ]
 

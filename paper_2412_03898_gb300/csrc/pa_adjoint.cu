@@ -44,10 +44,10 @@ constexpr int kAdjGroup = 4;
 // samples.  Returns the totals (identical in every lane).
 // Sensor coordinates are read from sens[c * sstr + s] (shared memory, or the
 // global sensor array of a batched scene).
+template <int G = kAdjGroup>
 __device__ __forceinline__ void ball_frame_grad(const Acq &q, const float *gframe, const float *sens, int sstr,
                                                 float4 *rec, int lane, float bx, float by, float bz, float a,
                                                 float p, float out[5], bool &dom) {
-  constexpr int G = kAdjGroup;
   const int S = q.S, T = q.T;
   float gx = 0.f, gy = 0.f, gz = 0.f, ga = 0.f, gp = 0.f;
   if (a > 0.f && p != 0.f) {
@@ -107,10 +107,8 @@ __device__ __forceinline__ void ball_frame_grad(const Acq &q, const float *gfram
 #pragma unroll
         for (int h = 0; h < G / 2; ++h) S1[h] = S3[h] = SR[h] = make_float2(0.f, 0.f);
         const float2 negk = make_float2(-K_2LN2, -K_2LN2), one = make_float2(1.f, 1.f);
-        for (int j = lane; j - lane < wmax; j += 32) {
-          float Gv[G];
-#pragma unroll
-          for (int q = 0; q < G; ++q) Gv[q] = j < Wq[q] ? __ldg(gq[q] + j) : 0.f;
+        // one 32-sample step of all G pairs, given their residual values
+        auto step = [&](const float (&Gv)[G]) {
 #pragma unroll
           for (int h = 0; h < G / 2; ++h) {
             const float2 sq = __fmul2_rn(u2[h], u2[h]);                       // u^2
@@ -122,6 +120,27 @@ __device__ __forceinline__ void ball_frame_grad(const Acq &q, const float *gfram
             SR[h] = __ffma2_rn(ge, __ffma2_rn(sq, negk, one), SR[h]);         // sum g E (1 - tau^2/a^2)
             u2[h] = __fadd2_rn(u2[h], nd2[h]);
           }
+        };
+        // two steps per trip: their 2G residual loads are issued together
+        const int nit = (wmax + 31) >> 5;
+        int it = 0;
+        for (; it + 1 < nit; it += 2) {
+          const int j = 32 * it + lane;
+          float Ga[G], Gb[G];
+#pragma unroll
+          for (int q = 0; q < G; ++q) {
+            Ga[q] = j < Wq[q] ? __ldg(gq[q] + j) : 0.f;
+            Gb[q] = j + 32 < Wq[q] ? __ldg(gq[q] + j + 32) : 0.f;
+          }
+          step(Ga);
+          step(Gb);
+        }
+        if (it < nit) {
+          const int j = 32 * it + lane;
+          float Ga[G];
+#pragma unroll
+          for (int q = 0; q < G; ++q) Ga[q] = j < Wq[q] ? __ldg(gq[q] + j) : 0.f;
+          step(Ga);
         }
 #pragma unroll
         for (int q = 0; q < G; ++q) {
@@ -159,6 +178,7 @@ __device__ __forceinline__ void load_sensors(const AdjArgs &A, float *ssens) {
 }
 
 // Static mode: item = (frame, ball).
+template <int G>
 __global__ void __launch_bounds__(32 * kAdjWarps) k_adjoint_static(const AdjArgs A) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   float4 *recs = reinterpret_cast<float4 *>(smem_raw);
@@ -179,8 +199,8 @@ __global__ void __launch_bounds__(32 * kAdjWarps) k_adjoint_static(const AdjArgs
 #pragma unroll
     for (int c = 0; c < 5; ++c) v[c] = __shfl_sync(FULL, mine, c);
     float g[5];
-    ball_frame_grad(A.q, A.g + (long long)f * A.q.S * A.q.T, ssens, A.q.S, rec, lane, v[0], v[1], v[2], v[3], v[4],
-                    g, dom);
+    ball_frame_grad<G>(A.q, A.g + (long long)f * A.q.S * A.q.T, ssens, A.q.S, rec, lane, v[0], v[1], v[2], v[3],
+                       v[4], g, dom);
     const float sc = A.frame_scale ? __ldg(A.frame_scale + f) : 1.f;
     if (lane < 5) {
       float gv = g[0];
@@ -353,7 +373,8 @@ cudaError_t launch_gridstride(K kern, const AdjArgs &a, size_t smem, int sms, cu
 
 cudaError_t launch_adjoint_static(const AdjArgs &a, int sms, cudaStream_t st) {
   if (a.n_items == 0) return cudaSuccess;
-  return launch_gridstride(k_adjoint_static, a, adj_static_smem(a.q.S), sms, st);
+  // 4 pairs per group measured fastest on the static 100k-ball workload (2 and 8 slower)
+  return launch_gridstride(k_adjoint_static<kAdjGroup>, a, adj_static_smem(a.q.S), sms, st);
 }
 
 cudaError_t launch_adjoint_batched(const BatchAdjArgs &a, int sms, cudaStream_t st) {

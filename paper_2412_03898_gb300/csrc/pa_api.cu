@@ -467,4 +467,22 @@ int32_t pa_adam_step(float *x, const float *g, float *m, float *v, int64_t n, do
                                      (float)(1.0 - beta2), (float)eps, bc1, bc2, static_cast<cudaStream_t>(stream)));
 }
 
+int32_t pa_adam_step_scheduled(float *x, const float *g, float *m, float *v, int64_t n, double lr0, double beta1,
+                               double beta2, double eps, int32_t step_size, double gamma, const int32_t *step,
+                               void *stream) {
+  if (n < 0 || step_size < 1 || step == nullptr || !(beta1 >= 0.0 && beta1 < 1.0) ||
+      !(beta2 >= 0.0 && beta2 < 1.0) || !(eps > 0.0) || !(gamma > 0.0))
+    return PA_ERR_INVALID_ARG;
+  if (n == 0) return PA_OK;
+  if (!x || !g || !m || !v) return PA_ERR_INVALID_ARG;
+  return cuda_status(pa::launch_adam_sched(x, g, m, v, n, (float)lr0, (float)beta1, (float)beta2,
+                                           (float)(1.0 - beta1), (float)(1.0 - beta2), (float)eps, step_size,
+                                           (float)gamma, step, static_cast<cudaStream_t>(stream)));
+}
+
+int32_t pa_step_increment(int32_t *step, void *stream) {
+  if (step == nullptr) return PA_ERR_INVALID_ARG;
+  return cuda_status(pa::launch_step_increment(step, static_cast<cudaStream_t>(stream)));
+}
+
 }  // extern "C"

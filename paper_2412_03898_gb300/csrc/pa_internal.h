@@ -115,6 +115,10 @@ cudaError_t launch_loss(const float *pred, const float *meas, long long per_fram
                         const float *scale, double *loss, float *resid, double *partials,
                         int blocks_per_frame, cudaStream_t st);
 int loss_blocks_per_frame(long long per_frame);
+cudaError_t launch_adam_sched(float *x, const float *g, float *m, float *v, long long n, float lr0, float b1,
+                              float b2, float omb1, float omb2, float eps, int step_size, float gamma,
+                              const int *step, cudaStream_t st);
+cudaError_t launch_step_increment(int *step, cudaStream_t st);
 cudaError_t launch_adam(float *x, const float *g, float *m, float *v, long long n, float lr, float b1,
                         float b2, float omb1, float omb2, float eps, float bc1, float bc2, cudaStream_t st);
 

@@ -131,7 +131,43 @@ __global__ void k_adam_tail(float *x, const float *g, float *m, float *v, long l
   x[i] -= lr * (m[i] / bc1) / (sqrtf(v[i] / bc2) + eps);
 }
 
+// Adam with t = *step from device memory (see pa_adam_step_scheduled).
+__global__ void k_adam_sched(float *__restrict__ x, const float *__restrict__ g, float *__restrict__ m,
+                             float *__restrict__ v, long long n, float lr0, float b1, float b2, float omb1, float omb2,
+                             float eps, int step_size, float gamma, const int *__restrict__ step) {
+  const int t = max(*step, 1);
+  const float lr = lr0 * powf(gamma, (float)((t - 1) / step_size));
+  const float bc1 = 1.f - powf(b1, (float)t);
+  const float bc2 = 1.f - powf(b2, (float)t);
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n;
+       i += (long long)gridDim.x * blockDim.x) {
+    const float gi = g[i];
+    const float mi = fmaf(b1, m[i], omb1 * gi);
+    const float vi = fmaf(b2, v[i], omb2 * gi * gi);
+    m[i] = mi;
+    v[i] = vi;
+    x[i] -= lr * (mi / bc1) / (sqrtf(vi / bc2) + eps);
+  }
+}
+
+__global__ void k_step_increment(int *step) { *step += 1; }
+
 }  // namespace
+
+cudaError_t launch_adam_sched(float *x, const float *g, float *m, float *v, long long n, float lr0, float b1,
+                              float b2, float omb1, float omb2, float eps, int step_size, float gamma,
+                              const int *step, cudaStream_t st) {
+  if (n == 0) return cudaSuccess;
+  const long long blocks = std::min<long long>((n + 255) / 256, 152LL * 16);
+  k_adam_sched<<<(unsigned)blocks, 256, 0, st>>>(x, g, m, v, n, lr0, b1, b2, omb1, omb2, eps, step_size, gamma,
+                                                 step);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_step_increment(int *step, cudaStream_t st) {
+  k_step_increment<<<1, 1, 0, st>>>(step);
+  return cudaGetLastError();
+}
 
 cudaError_t launch_deform(const float *canon, const float *omega, const float *theta, const float *sigma,
                           long long n, long long stride, int nb, const float *t, int F, float *out, unsigned *err,

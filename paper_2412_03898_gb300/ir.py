@@ -8,9 +8,11 @@ learning rates and step decay (step_size 160, drop 0.1).  The optimiser type
 is not named in the paper; Adam is this library's reading.
 
 Two execution forms of the same iteration:
-  - batched: all frames in one launch per kernel; the launch sequence of the
-    deform/forward/loss/adjoint part is captured once in a CUDA graph and
-    replayed (step_graph);
+  - batched: all frames in one launch per kernel; the whole iteration
+    (deform, forward, loss, adjoint, step counter, Adam) is captured once in
+    a CUDA graph and replayed (step_graph).  The Adam step number lives in
+    device memory, so the decayed learning rate and bias corrections need no
+    host scalars;
   - per-frame: F plain launch sequences, one frame each, gradients
     accumulated across frames (step_per_frame).
 """
@@ -21,7 +23,7 @@ from typing import Optional
 
 import torch
 
-from . import Geometry, adam_step, adjoint, deform_balls, forward, residual_loss
+from . import Geometry, adam_step_scheduled, adjoint, deform_balls, forward, residual_loss, step_increment
 
 # Sec. 3.2: initial learning rates and step decay.
 LR_COORD = 5e-7
@@ -59,6 +61,7 @@ class GGBallIR:
         self.resid = torch.empty_like(self.traces)
         self.loss = torch.empty(self.F, dtype=torch.float64, device=dev)
         self.step_count = 0
+        self.step_dev = torch.zeros(1, dtype=torch.int32, device=dev)
         self.graph: Optional[torch.cuda.CUDAGraph] = None
         self._fws = None
         self._lws = torch.empty(1 << 20, dtype=torch.uint8, device=dev)
@@ -79,24 +82,27 @@ class GGBallIR:
                 sigma=self.deform[2], t_frames=self.t, n=self.n, out=self._grads_tuple())
 
     def lr_scale(self) -> float:
-        return DROP_RATE ** (self.step_count // STEP_SIZE)
+        """Step decay of Sec. 3.2 for the iteration last taken (1-based t):
+        DROP_RATE ** floor((t - 1) / STEP_SIZE)."""
+        return DROP_RATE ** (max(self.step_count - 1, 0) // STEP_SIZE)
 
     def _adam(self):
+        # one device-side step counter; every group reads t from it
+        step_increment(self.step_dev)
         self.step_count += 1
-        k = self.lr_scale()
-        stride = self.canon.shape[-1]
-        # x, y, z and a rows share one launch when their rates agree (both 5e-7)
-        assert LR_COORD == LR_STD
-        adam_step(self.canon[:4].view(-1), self.g_canon[:4].reshape(-1), self.m_canon[:4].view(-1),
-                  self.v_canon[:4].view(-1), LR_COORD * k, self.step_count)
-        adam_step(self.canon[4], self.g_canon[4], self.m_canon[4], self.v_canon[4], LR_PRESSURE * k, self.step_count)
-        adam_step(self.deform.view(-1), self.g_deform.view(-1), self.m_deform.view(-1), self.v_deform.view(-1),
-                  LR_DEFORM * k, self.step_count)
-        del stride
+        assert LR_COORD == LR_STD  # x, y, z and a rows share one launch
+        for lr0, x, g, m, v in (
+                (LR_COORD, self.canon[:4], self.g_canon[:4], self.m_canon[:4], self.v_canon[:4]),
+                (LR_PRESSURE, self.canon[4], self.g_canon[4], self.m_canon[4], self.v_canon[4]),
+                (LR_DEFORM, self.deform, self.g_deform, self.m_deform, self.v_deform)):
+            adam_step_scheduled(x.reshape(-1), g.reshape(-1), m.reshape(-1), v.reshape(-1), lr0, self.step_dev,
+                                STEP_SIZE, DROP_RATE)
 
     def _ensure_workspace(self):
         from . import forward_workspace_size
-        need = forward_workspace_size(self.geom, self.state, self.n)
+        # all frames at once (batched) and one frame (per-frame form)
+        need = max(forward_workspace_size(self.geom, self.state, self.n),
+                   forward_workspace_size(self.geom, self.state[:1], self.n))
         if need > 0 and (self._fws is None or self._fws.numel() < need):
             self._fws = torch.empty(need, dtype=torch.uint8, device=self.canon.device)
 
@@ -108,25 +114,33 @@ class GGBallIR:
         self._adam()
         return self.loss
 
+    def _iteration(self):
+        self._forward_loss_adjoint()
+        self._adam()
+
     def capture(self) -> None:
-        """Capture the deform/forward/loss/adjoint launches in a CUDA graph."""
+        """Capture one whole iteration in a CUDA graph.  The capture itself
+        does not run the iteration; the warm-up iteration before it does."""
         self._ensure_workspace()
         s = torch.cuda.Stream()
         s.wait_stream(torch.cuda.current_stream())
         with torch.cuda.stream(s):
-            self._forward_loss_adjoint()  # warm-up on the capture stream
+            self._iteration()  # warm-up (a real iteration)
         torch.cuda.current_stream().wait_stream(s)
         g = torch.cuda.CUDAGraph()
+        count = self.step_count
         with torch.cuda.graph(g):
-            self._forward_loss_adjoint()
+            self._iteration()
+        self.step_count = count  # capture recorded, did not run
         self.graph = g
 
     def step_graph(self) -> torch.Tensor:
-        """One batched IR iteration: graph replay + Adam."""
+        """One batched IR iteration replayed from the graph."""
         if self.graph is None:
             self.capture()
+            return self.loss
         self.graph.replay()
-        self._adam()
+        self.step_count += 1
         return self.loss
 
     def step_per_frame(self) -> torch.Tensor:
@@ -149,7 +163,7 @@ class GGBallIR:
         p = forward_plan(self.geom, self.state[:1] if per_frame else self.state, self.n)
         fwd = 1 + (1 if p["n_splits"] > 1 else 0)
         core = 1 + fwd + 2 + 1  # deform, forward(+split reduce), loss partial+final, adjoint
-        adam = 3
+        adam = 4  # step counter + three parameter groups
         return (core * self.F if per_frame else core) + adam
 
 
