@@ -82,18 +82,31 @@ def pad_last(x: torch.Tensor, stride: Optional[int] = None) -> torch.Tensor:
 class Geometry:
     """Sensor array and acquisition scalars (pa_geom)."""
 
-    def __init__(self, sensors: torch.Tensor, c: float, fs: float, t0: float, n_samples: int, kappa: float = 5.0):
+    def __init__(self, sensors: torch.Tensor, c: float, fs: float, t0: float, n_samples: int, kappa: float = 5.0,
+                 sensor_range: Optional[tuple] = None):
+        """sensors: [3, S] CUDA float32.  sensor_range = (begin, end) selects a
+        shard of the array without copying (the pointer is offset and the row
+        stride stays S): outputs then cover sensors begin..end-1 only."""
         self.sensors = _check(sensors, "sensors")
         if sensors.dim() != 2 or sensors.shape[0] != 3:
             raise ValueError("sensors must be [3, S]")
         self.c, self.fs, self.t0 = float(c), float(fs), float(t0)
         self.n_samples, self.kappa = int(n_samples), float(kappa)
-        self._struct = _lib.pa_geom(self.sensors.data_ptr(), self.n_sensors, self.n_sensors, self.c, self.fs,
-                                    self.t0, self.n_samples, self.kappa)
+        total = int(sensors.shape[1])
+        b, e = (0, total) if sensor_range is None else (int(sensor_range[0]), int(sensor_range[1]))
+        if not 0 <= b < e <= total:
+            raise ValueError("sensor_range must satisfy 0 <= begin < end <= S")
+        self.sensor_range = (b, e)
+        self._struct = _lib.pa_geom(self.sensors.data_ptr() + 4 * b, e - b, total, self.c, self.fs, self.t0,
+                                    self.n_samples, self.kappa)
 
     @property
     def n_sensors(self) -> int:
-        return int(self.sensors.shape[1])
+        return self.sensor_range[1] - self.sensor_range[0]
+
+    def shard(self, begin: int, end: int) -> "Geometry":
+        """The same acquisition restricted to sensors begin..end-1."""
+        return Geometry(self.sensors, self.c, self.fs, self.t0, self.n_samples, self.kappa, (begin, end))
 
     def struct(self) -> _lib.pa_geom:
         return self._struct

@@ -19,8 +19,8 @@ from . import Geometry, forward, forward_batched, forward_plan, forward_workspac
 
 # (s_tile, t_tile, nb_tile, splits, group); splits 0 = the planner's choice
 DEFAULT_CANDIDATES = [
-    (12, 4096, 512, 0, 8), (12, 4096, 256, 0, 8), (16, 2048, 256, 0, 8), (16, 2048, 512, 0, 8), (16, 2048, 128, 0, 8), (8, 2048, 256, 0, 8),
-    (8, 4096, 512, 0, 8), (4, 4096, 256, 0, 8), (16, 2048, 256, 0, 4), (12, 2048, 256, 0, 8),
+    (12, 2048, 512, 0, 8), (12, 2048, 256, 0, 8), (6, 4096, 512, 0, 8), (8, 2048, 256, 0, 8),
+    (16, 1024, 256, 0, 8), (12, 2048, 256, 0, 4), (6, 4096, 256, 0, 8), (4, 4096, 256, 0, 8),
 ]
 
 _cache: dict = {}
@@ -113,7 +113,7 @@ def tune_batched(scenes, candidates: Optional[Sequence[tuple]] = None, reps: int
     cands = []
     for c in (candidates or DEFAULT_CANDIDATES):
         s_tile, t_tile, nb = c[0], c[1], c[2]
-        smem = 128 + 4 * 2 * 5 * nb + 16 * 32 * s_tile + 4 * s_tile * t_tile
+        smem = 128 + 4 * 2 * 5 * nb + 16 * 32 * s_tile + 8 * s_tile * t_tile
         if smem <= smem_max:
             cands.append(c)
     flush = torch.empty(64 * 1024 * 1024, dtype=torch.float32, device=dev)

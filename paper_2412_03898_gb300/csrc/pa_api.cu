@@ -317,10 +317,10 @@ int32_t pa_forward_batched(const pa_scene *scenes, int32_t n_scenes, uint32_t fl
     if (sc.n_frames > 0 && (sc.traces == nullptr || !aligned(sc.traces, 16))) return PA_ERR_INVALID_ARG;
     maxT = std::max(maxT, sc.geom.n_samples);
   }
-  const int s_tile = tiles && tiles[0] > 0 ? tiles[0] : 16;
   int t_tile = tiles && tiles[1] > 0 ? tiles[1] : 2048;
   t_tile = std::min(std::min(t_tile, maxT), 16384);
-  const int nb_tile = tiles && tiles[2] > 0 ? tiles[2] : 256;
+  const int nb_tile = tiles && tiles[2] > 0 ? tiles[2] : 512;
+  const int s_tile = tiles && tiles[0] > 0 ? tiles[0] : pa::forward_default_s_tile(t_tile, nb_tile);
   const int group = tiles && tiles[4] == 4 ? 4 : 8;
   const size_t smem = pa::forward_smem_bytes(s_tile, t_tile, nb_tile);
   if ((long long)smem > d->max_smem) return PA_ERR_INVALID_ARG;

@@ -37,15 +37,17 @@ struct FwdSmem {
   uint64_t *bars;  // 2 mbarriers (TMA stages)
   float *sball;    // [2][5][nb_tile] ball tiles
   float4 *srec;    // [s_tile][32] pair records
-  float *str;      // [s_tile][t_tile] trace tiles
+  float *str;      // [s_tile][t_tile] trace tiles (high part)
+  float *strlo;    // [s_tile][t_tile] rounding errors of str (compensated sum)
 };
 
-__device__ __forceinline__ FwdSmem fwd_smem(unsigned char *raw, int s_tile, int nb_tile) {
+__device__ __forceinline__ FwdSmem fwd_smem(unsigned char *raw, int s_tile, int t_tile, int nb_tile) {
   FwdSmem m;
   m.bars = reinterpret_cast<uint64_t *>(raw);
   m.sball = reinterpret_cast<float *>(raw + 128);
   m.srec = reinterpret_cast<float4 *>(m.sball + 2 * 5 * nb_tile);
   m.str = reinterpret_cast<float *>(m.srec + s_tile * 32);
+  m.strlo = m.str + s_tile * t_tile;
   return m;
 }
 
@@ -69,7 +71,7 @@ __device__ __forceinline__ bool forward_item(const Acq &q, const float *state_f,
 
   __syncthreads();  // the previous item (if any) is done with the trace tiles
   float4 *str4 = reinterpret_cast<float4 *>(m.str);
-  const int nz = s_tile * t_tile / 4;
+  const int nz = 2 * s_tile * t_tile / 4;  // high and low parts
   for (int i = tid; i < nz; i += blockDim.x) str4[i] = make_float4(0.f, 0.f, 0.f, 0.f);
 
   auto issue = [&](int t) {
@@ -96,6 +98,7 @@ __device__ __forceinline__ bool forward_item(const Acq &q, const float *state_f,
     sz = q.sensors[2 * q.sstride + s];
   }
   float *mytr = m.str + warp * t_tile;
+  float *mylo = m.strlo + warp * t_tile;
   float4 *myrec = m.srec + warp * 32;
   bool dom = false;
   // window bound in scaled units: |u| <= kappa K_S (Gaussian), |u| <= 1 (uniform)
@@ -132,35 +135,35 @@ __device__ __forceinline__ bool forward_item(const Acq &q, const float *state_f,
         const bool valid = w.W > 0;
         const int nv = __popc(__ballot_sync(FULL, valid));
         if (nv == 0) continue;
-        if (valid) myrec[lane] = make_float4(w.u0, w.du, w.amp, __int_as_float((w.klo - k0) | (w.W << 16)));
+        // every lane publishes a record; an invalid pair's record is a pad far
+        // outside every window with zero amplitude (kl = 0xffff, kend = 0, so
+        // it never widens a group's sample range)
+        myrec[lane] = valid ? make_float4(w.u0, w.du, w.amp, __int_as_float((w.klo - k0) | ((w.klo - k0 + w.W - 1) << 16)))
+                            : make_float4(1e30f, 0.f, 0.f, __int_as_float(0xffff));
         // sort by first sample; invalid pairs last; lane index in the low bits
         const unsigned key = warp_sort(((valid ? (unsigned)(w.klo - k0) : 0xffffu) << 5) | (unsigned)lane, lane);
         __syncwarp();
         for (int g0 = 0; g0 < nv; g0 += G) {
           float uq[G], duq[G], aq[G];
           int klq[G];
-          int kmin = 0x7fffffff, kmax = -1;
+          int kmin = 0xffff, kmax = -1;
 #pragma unroll
           for (int q = 0; q < G; ++q) {
+            // positions past nv hold pads (sorted last)
             const int src = (int)(__shfl_sync(FULL, key, (g0 + q) & 31) & 31u);
-            const bool act = g0 + q < nv;
             const float4 r = myrec[src];
             const int pk = __float_as_int(r.w);
-            const int kl = pk & 0xffff, W = pk >> 16;
-            if (act) {
-              kmin = min(kmin, kl);
-              kmax = max(kmax, kl + W - 1);
-            }
-            // inactive slots: far outside every window, zero amplitude
-            uq[q] = act ? r.x : 1e30f;
-            duq[q] = act ? r.y : 0.f;
-            aq[q] = act ? r.z : 0.f;
-            klq[q] = act ? kl : 0;
+            klq[q] = pk & 0xffff;
+            kmin = min(kmin, klq[q]);
+            kmax = max(kmax, pk >> 16);
+            uq[q] = r.x;
+            duq[q] = r.y;
+            aq[q] = r.z;
           }
           // balls in twos: u, its step and amp*u of two balls share one packed
           // FP32x2 instruction.  u starts at this lane's first sample
           // kmin + lane; the offset from the pair's own first sample is a small
-          // exact integer.
+          // exact integer (pads stay far outside every window).
           float2 u2[(G + 1) / 2], nd2[(G + 1) / 2], amp2[(G + 1) / 2];
 #pragma unroll
           for (int h = 0; h < (G + 1) / 2; ++h) {
@@ -174,17 +177,33 @@ __device__ __forceinline__ bool forward_item(const Acq &q, const float *state_f,
           for (int base = kmin; base <= kmax; base += 32) {
             const int k = base + lane;
             if (k <= kmax) {
-              float t = mytr[k];
+              // the group's pulses at this sample, summed in registers (one
+              // partial sum per ball pair keeps the dependency chains short)
+              float tp[(G + 1) / 2];
 #pragma unroll
               for (int h = 0; h < (G + 1) / 2; ++h) {
                 const float2 sq = __fmul2_rn(u2[h], u2[h]);
                 const float2 w = __fmul2_rn(amp2[h], u2[h]);
                 const float ex = UNIFORM ? 1.f : ex2(-sq.x);
                 const float ey = UNIFORM ? 1.f : ex2(-sq.y);
-                if (sq.x <= umax2) t = fmaf(w.x, ex, t);
-                if (sq.y <= umax2) t = fmaf(w.y, ey, t);
+                float th = sq.x <= umax2 ? w.x * ex : 0.f;
+                if (sq.y <= umax2) th = fmaf(w.y, ey, th);
+                tp[h] = th;
               }
-              mytr[k] = t;
+#pragma unroll
+              for (int st = 1; st < (G + 1) / 2; st *= 2)
+#pragma unroll
+                for (int h = 0; h + st < (G + 1) / 2; h += 2 * st) tp[h] += tp[h + st];
+              const float t = tp[0];
+              // compensated accumulation: a sample collects the cancelling
+              // pulses of thousands of balls, and a plain FP32 running sum
+              // loses ~1e-5 relative by 1e5 balls.  Dekker's FastTwoSum is
+              // exact when |running sum| >= |t|, which holds after the first
+              // few groups; otherwise its error term loses about eps |t|.
+              float hs, he;
+              fast_two_sum(mytr[k], t, hs, he);
+              mytr[k] = hs;
+              mylo[k] += he;
             }
 #pragma unroll
             for (int h = 0; h < (G + 1) / 2; ++h) u2[h] = __fadd2_rn(u2[h], nd2[h]);
@@ -215,8 +234,14 @@ __device__ __forceinline__ bool forward_item(const Acq &q, const float *state_f,
   if (s_ok) {
     float4 *d4 = reinterpret_cast<float4 *>(dst_f + (long long)s * T + k0);
     const float4 *s4 = reinterpret_cast<const float4 *>(mytr);
+    const float4 *l4 = reinterpret_cast<const float4 *>(mylo);
     for (int i = lane; i < klen / 4; i += 32) {
       float4 v = s4[i];
+      const float4 lo = l4[i];
+      v.x += lo.x;
+      v.y += lo.y;
+      v.z += lo.z;
+      v.w += lo.w;
       if (acc) {
         const float4 o = d4[i];
         v.x += o.x;
@@ -243,7 +268,7 @@ __device__ __forceinline__ void init_bars(uint64_t *bars) {
 template <bool UNIFORM, int G>
 __global__ void __launch_bounds__(kMaxThreads, 1) k_forward(const FwdArgs A) {
   extern __shared__ __align__(128) unsigned char smem_raw[];
-  const FwdSmem m = fwd_smem(smem_raw, A.s_tile, A.nb_tile);
+  const FwdSmem m = fwd_smem(smem_raw, A.s_tile, A.t_tile, A.nb_tile);
   init_bars(m.bars);
   int item = blockIdx.x;
   const int split = item % A.n_splits;
@@ -272,7 +297,7 @@ __global__ void __launch_bounds__(kMaxThreads, 1) k_forward(const FwdArgs A) {
 template <int G>
 __global__ void __launch_bounds__(kMaxThreads, 1) k_forward_batched(const BatchFwdArgs A) {
   extern __shared__ __align__(128) unsigned char smem_raw[];
-  const FwdSmem m = fwd_smem(smem_raw, A.s_tile, A.nb_tile);
+  const FwdSmem m = fwd_smem(smem_raw, A.s_tile, A.t_tile, A.nb_tile);
   __shared__ long long s_item;
   init_bars(m.bars);
   unsigned phase = 0;
@@ -298,20 +323,28 @@ __global__ void __launch_bounds__(kMaxThreads, 1) k_forward_batched(const BatchF
   }
 }
 
-// out[i] (+)= sum over splits of partial[split][i], splits in order.
+// out[i] (+)= sum over splits of partial[split][i], splits in order, with
+// compensated (TwoSum) accumulation: partials of different ball ranges can
+// cancel each other.
 __global__ void k_reduce_splits(const float4 *__restrict__ partial, float4 *__restrict__ out,
                                 long long n4, int n_splits, bool accumulate) {
   for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n4;
        i += (long long)gridDim.x * blockDim.x) {
     float4 v = accumulate ? out[i] : make_float4(0.f, 0.f, 0.f, 0.f);
+    float4 e = make_float4(0.f, 0.f, 0.f, 0.f);
     for (int sp = 0; sp < n_splits; ++sp) {
       const float4 p = __ldg(&partial[sp * n4 + i]);
-      v.x += p.x;
-      v.y += p.y;
-      v.z += p.z;
-      v.w += p.w;
+      float r;
+      two_sum(v.x, p.x, v.x, r);
+      e.x += r;
+      two_sum(v.y, p.y, v.y, r);
+      e.y += r;
+      two_sum(v.z, p.z, v.z, r);
+      e.z += r;
+      two_sum(v.w, p.w, v.w, r);
+      e.w += r;
     }
-    out[i] = v;
+    out[i] = make_float4(v.x + e.x, v.y + e.y, v.z + e.z, v.w + e.w);
   }
 }
 
@@ -340,7 +373,7 @@ __global__ void k_count(const Acq q, const float *state, long long n, long long 
 
 size_t forward_smem_bytes(int s_tile, int t_tile, int nb_tile) {
   return 128 + sizeof(float) * (size_t)(2 * 5 * nb_tile) + sizeof(float4) * (size_t)(s_tile * 32) +
-         sizeof(float) * (size_t)s_tile * t_tile;
+         2 * sizeof(float) * (size_t)s_tile * t_tile;
 }
 
 namespace {
@@ -364,18 +397,25 @@ int forward_blocks_per_sm(const FwdPlan &p, bool uniform) {
   return nb;
 }
 
+int forward_default_s_tile(int t_tile, int nb_tile) {
+  const long long budget = 232448 - 128 - (long long)sizeof(float) * 2 * 5 * nb_tile;
+  const long long per_sensor = 2LL * (long long)sizeof(float) * t_tile + (long long)sizeof(float4) * 32;
+  return (int)std::max(1LL, std::min(16LL, budget / per_sensor));
+}
+
 FwdPlan forward_plan(int S, int T, long long n, int F, int sms, int s_tile_o, int t_tile_o,
                      int nb_tile_o, int splits_o, int group_o) {
   FwdPlan p{};
   p.group = (group_o == 1 || group_o == 2 || group_o == 4) ? group_o : 8;
-  p.s_tile = s_tile_o > 0 ? s_tile_o : 16;
-  // 16 warps x 2048 samples per CTA measured best on the static 100k-ball
-  // workload (one 150 KB CTA per SM, 16 warps).
-  int tt = t_tile_o > 0 ? t_tile_o : 2048;
+  // Default: up to 2048 samples per CTA, 512-ball TMA stages, and as many
+  // sensors (warps) as fit in 227 KB of shared memory with the compensated
+  // (high, low) trace tiles, at most 16: 12 x 2048 for 4096-sample traces.
+  int tt = t_tile_o > 0 ? t_tile_o : std::min(T, 2048);
   tt = std::min(std::min(tt, T), 16384);
   tt = (tt + 3) & ~3;
   p.t_tile = tt;
-  p.nb_tile = nb_tile_o > 0 ? nb_tile_o : 256;
+  p.nb_tile = nb_tile_o > 0 ? nb_tile_o : 512;
+  p.s_tile = s_tile_o > 0 ? s_tile_o : forward_default_s_tile(tt, p.nb_tile);
   p.n_stiles = (S + p.s_tile - 1) / p.s_tile;
   p.n_ttiles = (T + p.t_tile - 1) / p.t_tile;
   p.smem = forward_smem_bytes(p.s_tile, p.t_tile, p.nb_tile);

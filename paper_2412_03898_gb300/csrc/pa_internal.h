@@ -99,6 +99,8 @@ struct AdjArgs {
 FwdPlan forward_plan(int S, int T, long long n, int F, int sms, int s_tile_override,
                      int t_tile_override, int nb_tile_override, int splits_override, int group_override);
 size_t forward_smem_bytes(int s_tile, int t_tile, int nb_tile);
+// Most sensors per CTA (<= 16) whose compensated trace tiles fit in 227 KB.
+int forward_default_s_tile(int t_tile, int nb_tile);
 int forward_blocks_per_sm(const FwdPlan &p, bool uniform);
 
 cudaError_t launch_forward(const FwdArgs &a, const FwdPlan &p, bool uniform, cudaStream_t st);

@@ -36,7 +36,7 @@ def _states(sc):
 
 
 def test_forward_batched_equals_single_and_oracle(pa):
-    tiles = (16, 2048, 256, 1, 8)
+    tiles = (12, 2048, 256, 1, 8)
     scs = _scenes()
     batch = [pa.Scene(geometry(sc), dev_pad(_states(sc)), sc.n_balls) for sc in scs]
     pa.forward_batched(batch, tiles=tiles)

@@ -130,6 +130,20 @@ def test_count_contributions_matches_oracle(pa):
 
 
 @pytest.mark.slow
+def test_forward_full_size_single_split_accuracy(pa):
+    """One ball split: each trace sample accumulates ~2,000 cancelling pulses
+    of the 100k balls in one CTA; the compensated accumulation must keep the
+    traces within tolerance (a plain FP32 running sum measured 1.4e-5)."""
+    sc = pa_inputs.config_scene(2)
+    geom = geometry(sc)
+    y = pa.forward(geom, dev_pad(sc.balls)[None], sc.n_balls, tiles=(12, 2048, 512, 1, 8))
+    rng = np.random.default_rng(1)
+    pick = np.sort(rng.choice(sc.n_sensors, 8, replace=False))
+    y_o, _ = oracle.forward(sc.balls, sc.sensors[:, pick], sc.c, sc.fs, sc.t0, sc.n_samples, sc.kappa)
+    assert rel_l2(y[0, pick].cpu().numpy(), y_o[0]) <= TRACE_TOL
+
+
+@pytest.mark.slow
 def test_forward_full_size_sampled_sensors(pa):
     """Static 100k-ball vessel tree, 576 sensors, T = 4096 in the bench's
     launch configuration; 12 random sensors checked against the oracle."""
