@@ -124,7 +124,7 @@ typedef struct pa_scene {
     pa_balls balls;          /* device [n_frames][5][stride] */
     int32_t n_frames;
     float *traces;           /* pa_forward_batched output, device [n_frames][S][T], 16-byte aligned */
-    const float *trace_grad; /* pa_adjoint_batched input, device [n_frames][S][T] */
+    const float *trace_grad; /* pa_adjoint_batched input, device [n_frames][S][T], 16-byte aligned */
     float *grad_state;       /* pa_adjoint_batched output, device [n_frames][5][stride] */
 } pa_scene;
 
@@ -169,7 +169,7 @@ PA_API int32_t pa_forward(const pa_geom *geom, const pa_balls *balls, int32_t n_
 /* pa_forward with an explicit tile plan, for autotuning.  tiles = {sensors
  * per CTA (1..16, 0 = default), samples per CTA (multiple of 4, 0 = default),
  * balls per TMA stage (multiple of 4, 0 = default), ball splits (0 =
- * default), pairs swept together per warp (1, 2, 4 or 8; 0 = default)}, a
+ * default), pairs swept together per warp (1, 2, 4, 8 or 16; 0 = default)}, a
  * host array of 5, or NULL for the built-in heuristic.  Results equal
  * pa_forward's up to float summation order. */
 PA_API size_t pa_forward_workspace_size_ex(const pa_geom *geom, const pa_balls *balls, int32_t n_frames,
@@ -186,7 +186,8 @@ PA_API int32_t pa_forward_plan_info(const pa_geom *geom, const pa_balls *balls, 
 
 /* Adjoint of pa_forward (gradients of the L2 loss, Sec. 2.2, last paragraph:
  * all baseline attributes and all (theta, sigma, omega) are learnable).
- * Given trace_grad = dL/dy, device [n_frames][n_sensors][n_samples], and an
+ * Given trace_grad = dL/dy, device [n_frames][n_sensors][n_samples] (16-byte
+ * aligned, read as float pairs), and an
  * optional per-frame scale (device [n_frames] or NULL = 1) applied to it:
  *  - static mode (balls != NULL, canon == NULL): grads->state receives
  *    dL/d(x, y, z, a, p) per frame;

@@ -19,8 +19,8 @@ from . import Geometry, forward, forward_batched, forward_plan, forward_workspac
 
 # (s_tile, t_tile, nb_tile, splits, group); splits 0 = the planner's choice
 DEFAULT_CANDIDATES = [
-    (12, 2048, 512, 0, 8), (12, 2048, 256, 0, 8), (6, 4096, 512, 0, 8), (8, 2048, 256, 0, 8),
-    (16, 1024, 256, 0, 8), (12, 2048, 256, 0, 4), (6, 4096, 256, 0, 8), (4, 4096, 256, 0, 8),
+    (16, 1536, 512, 0, 8), (16, 1536, 512, 0, 16), (12, 2048, 512, 0, 8), (12, 2048, 512, 0, 16),
+    (16, 1536, 256, 0, 8), (16, 1024, 512, 0, 8), (8, 2048, 512, 0, 8), (16, 1536, 512, 0, 4),
 ]
 
 _cache: dict = {}

@@ -7,13 +7,14 @@
 //  - One warp owns one ball (static mode: one (frame, ball) item) and loops
 //    over all sensors.  The 32 lanes compute the window, phase and gradient
 //    factors of 32 (ball, sensor) pairs in parallel and publish them,
-//    compacted, in shared memory; the warp then walks the windows of
-//    kAdjGroup pairs at a time in lockstep with lanes on consecutive samples,
-//    so that kAdjGroup independent coalesced residual loads g[f][s][k] (L2
-//    resident) are in flight per step, and accumulates per lane and pair
+//    compacted, in shared memory; the warp then walks four pairs at a time,
+//    one per 8-lane sub-warp, each lane on two consecutive samples per step
+//    (a float2 residual load from L2, packed FP32x2 arithmetic, next step's
+//    load in flight), accumulating per lane
 //        S1 = sum g E u,  S3 = sum g E u^3,  SR = sum g E (1 - tau^2/a^2)
-//    (two sensors per packed FP32x2 instruction)
-//    which the per-pair factors fold into per-lane gradient accumulators.
+//    which an 8-lane shuffle reduction turns into the pair's sums; the
+//    sub-warp's first lane folds them with the pair's factors into its
+//    gradient accumulators.
 //  - A warp-shuffle reduction over lanes (i.e. over sensors and samples) at
 //    the end of the ball gives dL/d(x, y, z, a, p); one lane writes it.
 //  - 4D mode recomputes the deformed state of the ball per frame in registers
@@ -36,15 +37,10 @@ namespace {
 
 constexpr int kAdjWarps = 8;
 
-// Pairs walked together per warp in the window loop: their residual loads are
-// independent, so G of them are in flight per warp and step.
-constexpr int kAdjGroup = 4;
-
 // dL/d(x, y, z, a, p) of one ball at frame f, summed over all sensors and
 // samples.  Returns the totals (identical in every lane).
 // Sensor coordinates are read from sens[c * sstr + s] (shared memory, or the
 // global sensor array of a batched scene).
-template <int G = kAdjGroup>
 __device__ __forceinline__ void ball_frame_grad(const Acq &q, const float *gframe, const float *sens, int sstr,
                                                 float4 *rec, int lane, float bx, float by, float bz, float a,
                                                 float p, float out[5], bool &dom) {
@@ -79,84 +75,66 @@ __device__ __forceinline__ void ball_frame_grad(const Acq &q, const float *gfram
         rec[3 * pos + 2] = r2;
       }
       __syncwarp();
-      for (int g0 = 0; g0 < nv; g0 += G) {
-        const float *gq[G];
-        int Wq[G];
-        int wmax = 0;
-        // pairs in twos: the per-sample arithmetic of two sensors shares one
-        // packed FP32x2 instruction
-        float2 u2[G / 2], nd2[G / 2], S1[G / 2], S3[G / 2], SR[G / 2];
-#pragma unroll
-        for (int q = 0; q < G; ++q) {
-          const bool act = g0 + q < nv;
-          const int i = act ? g0 + q : 0;
-          const float4 a0 = rec[3 * i + 0], a2 = rec[3 * i + 2];
-          Wq[q] = act ? __float_as_int(a2.z) : 0;
-          wmax = max(wmax, Wq[q]);
-          gq[q] = gframe + (long long)__float_as_int(a2.w) * T + __float_as_int(a2.y);
-          const float u = act ? fmaf((float)lane, -a0.y, a0.x) : 0.f;
-          const float nd = act ? -32.f * a0.y : 0.f;
-          if (q & 1) {
-            u2[q / 2].y = u;
-            nd2[q / 2].y = nd;
-          } else {
-            u2[q / 2].x = u;
-            nd2[q / 2].x = nd;
-          }
-        }
-#pragma unroll
-        for (int h = 0; h < G / 2; ++h) S1[h] = S3[h] = SR[h] = make_float2(0.f, 0.f);
-        const float2 negk = make_float2(-K_2LN2, -K_2LN2), one = make_float2(1.f, 1.f);
-        // one 32-sample step of all G pairs, given their residual values
-        auto step = [&](const float (&Gv)[G]) {
-#pragma unroll
-          for (int h = 0; h < G / 2; ++h) {
-            const float2 sq = __fmul2_rn(u2[h], u2[h]);                       // u^2
-            const float2 E = make_float2(ex2(-sq.x), ex2(-sq.y));             // exp(-tau^2/(2a^2))
-            const float2 ge = __fmul2_rn(make_float2(Gv[2 * h], Gv[2 * h + 1]), E);
-            const float2 gu = __fmul2_rn(ge, u2[h]);
-            S1[h] = __fadd2_rn(S1[h], gu);                                    // sum g E u
-            S3[h] = __ffma2_rn(gu, sq, S3[h]);                                // sum g E u^3
-            SR[h] = __ffma2_rn(ge, __ffma2_rn(sq, negk, one), SR[h]);         // sum g E (1 - tau^2/a^2)
-            u2[h] = __fadd2_rn(u2[h], nd2[h]);
-          }
+      // Four pairs at a time, one per 8-lane sub-warp: each sub-warp walks its
+      // pair's whole window, each lane two consecutive samples per step
+      // (one float2 load and packed FP32x2 arithmetic), the next step's load
+      // issued before the current step's arithmetic.
+      const int sub = lane >> 3, sl = lane & 7;
+      const float2 negk = make_float2(-K_2LN2, -K_2LN2), one = make_float2(1.f, 1.f);
+      for (int g0 = 0; g0 < nv; g0 += 4) {
+        const int i = g0 + sub;
+        const bool act = i < nv;
+        const int ii = act ? i : 0;
+        const float4 a0 = rec[3 * ii + 0], a2 = rec[3 * ii + 2];
+        const int klo = __float_as_int(a2.y);
+        const int khi = act ? klo + __float_as_int(a2.z) - 1 : -1;
+        const int ka = klo & ~1;  // float2-aligned start (rows start 16-byte aligned, T % 4 == 0)
+        const float2 *row = reinterpret_cast<const float2 *>(gframe + (long long)__float_as_int(a2.w) * T);
+        const int nit = act ? ((khi - ka) >> 4) + 1 : 0;
+        const int nmax = __reduce_max_sync(FULL, nit);
+        int kk = ka + 2 * sl;
+        float2 u2;
+        u2.x = fmaf((float)(kk - klo), -a0.y, a0.x);
+        u2.y = u2.x - a0.y;
+        const float2 nd2 = make_float2(-16.f * a0.y, -16.f * a0.y);
+        float2 S1 = make_float2(0.f, 0.f), S3 = S1, SR = S1;
+        // residual at samples kk, kk+1 (zero outside [klo, khi]; kk <= khi
+        // implies kk + 1 <= T - 1 since kk is even and T - 1 odd)
+        auto fetch = [&](int k) {
+          float2 v = make_float2(0.f, 0.f);
+          if (k <= khi) v = __ldg(row + (k >> 1));
+          if (k < klo) v.x = 0.f;
+          if (k + 1 > khi) v.y = 0.f;
+          return v;
         };
-        // two steps per trip: their 2G residual loads are issued together
-        const int nit = (wmax + 31) >> 5;
-        int it = 0;
-        for (; it + 1 < nit; it += 2) {
-          const int j = 32 * it + lane;
-          float Ga[G], Gb[G];
-#pragma unroll
-          for (int q = 0; q < G; ++q) {
-            Ga[q] = j < Wq[q] ? __ldg(gq[q] + j) : 0.f;
-            Gb[q] = j + 32 < Wq[q] ? __ldg(gq[q] + j + 32) : 0.f;
-          }
-          step(Ga);
-          step(Gb);
+        float2 gcur = fetch(kk);
+        for (int it = 0; it < nmax; ++it, kk += 16) {
+          const float2 gnext = fetch(kk + 16);
+          const float2 sq = __fmul2_rn(u2, u2);                         // u^2
+          const float2 E = make_float2(ex2(-sq.x), ex2(-sq.y));         // exp(-tau^2/(2a^2))
+          const float2 ge = __fmul2_rn(gcur, E);
+          const float2 gu = __fmul2_rn(ge, u2);
+          S1 = __fadd2_rn(S1, gu);                                      // sum g E u
+          S3 = __ffma2_rn(gu, sq, S3);                                  // sum g E u^3
+          SR = __ffma2_rn(ge, __ffma2_rn(sq, negk, one), SR);           // sum g E (1 - tau^2/a^2)
+          u2 = __fadd2_rn(u2, nd2);
+          gcur = gnext;
         }
-        if (it < nit) {
-          const int j = 32 * it + lane;
-          float Ga[G];
+        float s1 = S1.x + S1.y, s3 = S3.x + S3.y, sr = SR.x + SR.y;
 #pragma unroll
-          for (int q = 0; q < G; ++q) Ga[q] = j < Wq[q] ? __ldg(gq[q] + j) : 0.f;
-          step(Ga);
+        for (int o = 4; o > 0; o >>= 1) {
+          s1 += __shfl_xor_sync(FULL, s1, o);
+          s3 += __shfl_xor_sync(FULL, s3, o);
+          sr += __shfl_xor_sync(FULL, sr, o);
         }
-#pragma unroll
-        for (int q = 0; q < G; ++q) {
-          if (g0 + q < nv) {
-            const int i = g0 + q;
-            const float4 a0 = rec[3 * i + 0], a1 = rec[3 * i + 1], a2 = rec[3 * i + 2];
-            const float s1 = (q & 1) ? S1[q / 2].y : S1[q / 2].x;
-            const float s3 = (q & 1) ? S3[q / 2].y : S3[q / 2].x;
-            const float sr = (q & 1) ? SR[q / 2].y : SR[q / 2].x;
-            gp = fmaf(s1, a0.z, gp);
-            ga = fmaf(s3, -a0.w, ga);  // record holds -A/K_S^3 for sum g E u (-u^2)
-            const float dR = fmaf(s1, a1.x, a1.y * sr);
-            gx = fmaf(dR, a1.z, gx);
-            gy = fmaf(dR, a1.w, gy);
-            gz = fmaf(dR, a2.x, gz);
-          }
+        if (sl == 0 && act) {
+          const float4 a1 = rec[3 * ii + 1];
+          gp = fmaf(s1, a0.z, gp);
+          ga = fmaf(s3, -a0.w, ga);  // record holds -A/K_S^3 for sum g E u (-u^2)
+          const float dR = fmaf(s1, a1.x, a1.y * sr);
+          gx = fmaf(dR, a1.z, gx);
+          gy = fmaf(dR, a1.w, gy);
+          gz = fmaf(dR, a2.x, gz);
         }
       }
       __syncwarp();
@@ -178,7 +156,6 @@ __device__ __forceinline__ void load_sensors(const AdjArgs &A, float *ssens) {
 }
 
 // Static mode: item = (frame, ball).
-template <int G>
 __global__ void __launch_bounds__(32 * kAdjWarps) k_adjoint_static(const AdjArgs A) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   float4 *recs = reinterpret_cast<float4 *>(smem_raw);
@@ -199,7 +176,7 @@ __global__ void __launch_bounds__(32 * kAdjWarps) k_adjoint_static(const AdjArgs
 #pragma unroll
     for (int c = 0; c < 5; ++c) v[c] = __shfl_sync(FULL, mine, c);
     float g[5];
-    ball_frame_grad<G>(A.q, A.g + (long long)f * A.q.S * A.q.T, ssens, A.q.S, rec, lane, v[0], v[1], v[2], v[3],
+    ball_frame_grad(A.q, A.g + (long long)f * A.q.S * A.q.T, ssens, A.q.S, rec, lane, v[0], v[1], v[2], v[3],
                        v[4], g, dom);
     const float sc = A.frame_scale ? __ldg(A.frame_scale + f) : 1.f;
     if (lane < 5) {
@@ -374,7 +351,7 @@ cudaError_t launch_gridstride(K kern, const AdjArgs &a, size_t smem, int sms, cu
 cudaError_t launch_adjoint_static(const AdjArgs &a, int sms, cudaStream_t st) {
   if (a.n_items == 0) return cudaSuccess;
   // 4 pairs per group measured fastest on the static 100k-ball workload (2 and 8 slower)
-  return launch_gridstride(k_adjoint_static<kAdjGroup>, a, adj_static_smem(a.q.S), sms, st);
+  return launch_gridstride(k_adjoint_static, a, adj_static_smem(a.q.S), sms, st);
 }
 
 cudaError_t launch_adjoint_batched(const BatchAdjArgs &a, int sms, cudaStream_t st) {

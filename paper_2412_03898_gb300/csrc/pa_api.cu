@@ -103,7 +103,7 @@ int forward_impl(const pa_geom *geom, const pa_balls *balls, int32_t F, float *t
         cudaMemsetAsync(traces, 0, sizeof(float) * (size_t)F * geom->n_sensors * geom->n_samples, st));
   }
   if (tiles && (tiles[0] < 0 || tiles[0] > 16 || tiles[1] < 0 || tiles[2] < 0 || tiles[3] < 0 ||
-                (tiles[2] & 3) != 0 || (tiles[1] & 3) != 0 || tiles[4] < 0 || tiles[4] > 8))
+                (tiles[2] & 3) != 0 || (tiles[1] & 3) != 0 || tiles[4] < 0 || tiles[4] > 16))
     return PA_ERR_INVALID_ARG;
   const pa::FwdPlan p = pa::forward_plan(geom->n_sensors, geom->n_samples, balls->n, F, d->sms,
                                          tiles ? tiles[0] : 0, tiles ? tiles[1] : 0, tiles ? tiles[2] : 0,
@@ -205,7 +205,7 @@ int32_t pa_forward_ex(const pa_geom *geom, const pa_balls *balls, int32_t n_fram
 int32_t pa_forward_plan_info(const pa_geom *geom, const pa_balls *balls, int32_t n_frames, const int32_t *tiles,
                              int32_t *out7) {
   if (out7 == nullptr) return PA_ERR_INVALID_ARG;
-  if (tiles && (tiles[0] < 0 || tiles[0] > 16 || tiles[4] < 0 || tiles[4] > 8)) return PA_ERR_INVALID_ARG;
+  if (tiles && (tiles[0] < 0 || tiles[0] > 16 || tiles[4] < 0 || tiles[4] > 16)) return PA_ERR_INVALID_ARG;
   int rc = check_geom(geom);
   if (rc) return rc;
   if ((rc = check_balls(balls))) return rc;
@@ -244,7 +244,7 @@ int32_t pa_adjoint(const pa_geom *geom, const pa_balls *balls, const pa_canon *c
   }
   const long long n = four_d ? canon->n : balls->n;
   if (n == 0) return PA_OK;
-  if (n_frames > 0 && trace_grad == nullptr) return PA_ERR_INVALID_ARG;
+  if (n_frames > 0 && (trace_grad == nullptr || !aligned(trace_grad, 16))) return PA_ERR_INVALID_ARG;
   const DevInfo *d = dev_info();
   if (!d) return PA_ERR_CUDA;
   cudaStream_t st = static_cast<cudaStream_t>(stream);
@@ -317,7 +317,7 @@ int32_t pa_forward_batched(const pa_scene *scenes, int32_t n_scenes, uint32_t fl
     if (sc.n_frames > 0 && (sc.traces == nullptr || !aligned(sc.traces, 16))) return PA_ERR_INVALID_ARG;
     maxT = std::max(maxT, sc.geom.n_samples);
   }
-  int t_tile = tiles && tiles[1] > 0 ? tiles[1] : 2048;
+  int t_tile = tiles && tiles[1] > 0 ? tiles[1] : pa::kDefaultTTile;
   t_tile = std::min(std::min(t_tile, maxT), 16384);
   const int nb_tile = tiles && tiles[2] > 0 ? tiles[2] : 512;
   const int s_tile = tiles && tiles[0] > 0 ? tiles[0] : pa::forward_default_s_tile(t_tile, nb_tile);
@@ -366,6 +366,15 @@ int32_t pa_forward_batched(const pa_scene *scenes, int32_t n_scenes, uint32_t fl
   }
   a.total_items = items;
   if (items == 0) return PA_OK;
+  // CTAs write only the sample band a scene's balls reach: zero the rest first
+  if (!(flags & PA_ACCUMULATE)) {
+    for (int j = 0; j < m; ++j) {
+      const pa_scene &sc = scenes[order[j]];
+      cudaError_t e = cudaMemsetAsync(
+          sc.traces, 0, sizeof(float) * (size_t)sc.n_frames * sc.geom.n_sensors * sc.geom.n_samples, st);
+      if (e != cudaSuccess) return PA_ERR_CUDA;
+    }
+  }
   return cuda_status(pa::launch_forward_batched(a, group, smem, d->sms, st));
 }
 
@@ -386,7 +395,7 @@ int32_t pa_adjoint_batched(const pa_scene *scenes, int32_t n_scenes, uint32_t fl
     if ((rc = check_balls(&sc.balls))) return rc;
     if (sc.n_frames < 0) return PA_ERR_INVALID_ARG;
     if (sc.n_frames == 0 || sc.balls.n == 0) continue;
-    if (sc.trace_grad == nullptr || sc.grad_state == nullptr) return PA_ERR_INVALID_ARG;
+    if (sc.trace_grad == nullptr || sc.grad_state == nullptr || !aligned(sc.trace_grad, 16)) return PA_ERR_INVALID_ARG;
     order[m++] = i;
   }
   std::sort(order, order + m,

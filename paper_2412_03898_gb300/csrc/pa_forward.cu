@@ -255,6 +255,92 @@ __device__ __forceinline__ bool forward_item(const Acq &q, const float *state_f,
   return true;
 }
 
+// First sample of sample tile `tt` when the CTA's tiles are laid over the band
+// where the pulses of balls [b_begin, b_end) arrive at sensors
+// [st*s_tile, st*s_tile + s_tile): the band runs from the nearest to the
+// farthest point of the active balls' bounding box, widened by the largest
+// window half-width and two samples.  Returns -1 when the tile holds no
+// arrival (the caller has zeroed the output).  Block-wide: every thread calls
+// it; `red` is shared scratch of at least 8 * (warps + 1) floats.
+template <bool UNIFORM>
+__device__ int band_tile_start(const Acq &q, const float *state_f, long long stride, long long b_begin,
+                               long long b_end, int s_tile, int st, int t_tile, int tt, float *red) {
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5, nw = blockDim.x >> 5;
+  const float INF = __int_as_float(0x7f800000);
+  float v[7] = {INF, INF, INF, -INF, -INF, -INF, 0.f};  // min xyz, max xyz, max a
+  for (long long b = b_begin + tid; b < b_end; b += blockDim.x) {
+    const float a = state_f[3 * stride + b], p = state_f[4 * stride + b];
+    if (a > 0.f && p != 0.f) {
+#pragma unroll
+      for (int c = 0; c < 3; ++c) {
+        const float x = state_f[c * stride + b];
+        v[c] = fminf(v[c], x);
+        v[3 + c] = fmaxf(v[3 + c], x);
+      }
+      v[6] = fmaxf(v[6], a);
+    }
+  }
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) {
+#pragma unroll
+    for (int c = 0; c < 3; ++c) v[c] = fminf(v[c], __shfl_xor_sync(FULL, v[c], o));
+#pragma unroll
+    for (int c = 3; c < 7; ++c) v[c] = fmaxf(v[c], __shfl_xor_sync(FULL, v[c], o));
+  }
+  if (lane == 0)
+#pragma unroll
+    for (int c = 0; c < 7; ++c) red[warp * 8 + c] = v[c];
+  __syncthreads();
+  if (tid < 7) {
+    float r = red[tid];
+    for (int w = 1; w < nw; ++w) r = tid < 3 ? fminf(r, red[w * 8 + tid]) : fmaxf(r, red[w * 8 + tid]);
+    red[nw * 8 + tid] = r;
+  }
+  __syncthreads();
+  float box[7];
+#pragma unroll
+  for (int c = 0; c < 7; ++c) box[c] = red[nw * 8 + c];
+  __syncthreads();  // red is reused below
+  // per warp: distances from its sensor to the box
+  const int s = st * s_tile + warp;
+  float dmin = INF, dmax = -INF;
+  if (s < q.S && box[6] > 0.f) {
+    float n2 = 0.f, f2 = 0.f;
+#pragma unroll
+    for (int c = 0; c < 3; ++c) {
+      const float sc = q.sensors[c * q.sstride + s];
+      const float dn = fmaxf(fmaxf(box[c] - sc, sc - box[3 + c]), 0.f);
+      const float df = fmaxf(fabsf(sc - box[c]), fabsf(sc - box[3 + c]));
+      n2 = fmaf(dn, dn, n2);
+      f2 = fmaf(df, df, f2);
+    }
+    dmin = sqrtf(n2);
+    dmax = sqrtf(f2);
+  }
+  if (lane == 0) {
+    red[warp * 2] = dmin;
+    red[warp * 2 + 1] = dmax;
+  }
+  __syncthreads();
+  float rmin = INF, rmax = -INF;
+  for (int w = 0; w < nw; ++w) {
+    rmin = fminf(rmin, red[w * 2]);
+    rmax = fmaxf(rmax, red[w * 2 + 1]);
+  }
+  __syncthreads();
+  if (!(rmax >= rmin)) return -1;  // no active ball or no sensor
+  const float h = (UNIFORM ? 1.f : q.kappa) * box[6];
+  const float lo = floorf((rmin - h - q.ct0h) * q.inv_delta) - 2.f;
+  const float hi = ceilf((rmax + h - q.ct0h) * q.inv_delta) + 2.f;
+  const int T = q.T;
+  if (!(hi >= 0.f) || !(lo <= (float)(T - 1))) return -1;
+  const int kb_lo = ((int)fmaxf(lo, 0.f)) & ~3;
+  const int kb_hi = (int)fminf(hi, (float)(T - 1));
+  const long long start = (long long)kb_lo + (long long)tt * t_tile;
+  if (start > kb_hi || start >= T) return -1;
+  return (int)start;
+}
+
 __device__ __forceinline__ void init_bars(uint64_t *bars) {
   if (threadIdx.x == 0) {
     mbar_init(&bars[0], 1);
@@ -278,10 +364,13 @@ __global__ void __launch_bounds__(kMaxThreads, 1) k_forward(const FwdArgs A) {
   const int st = item % A.n_stiles;
   const int f = item / A.n_stiles;
   const int T = A.q.T;
-  const int k0 = tt * A.t_tile;
-  const int klen = min(A.t_tile, T - k0);
   const long long b_begin = (long long)split * A.balls_per_split;
   const long long b_end = min(A.n, b_begin + A.balls_per_split);
+  const float *state_f0 = A.state + (long long)f * 5 * A.stride;
+  const int k0 = band_tile_start<UNIFORM>(A.q, state_f0, A.stride, b_begin, b_end, A.s_tile, st, A.t_tile, tt,
+                                          reinterpret_cast<float *>(m.srec));
+  if (k0 < 0) return;  // no arrival in this tile; the output was zeroed
+  const int klen = min(A.t_tile, T - k0);
   const bool single = A.n_splits == 1;
   float *dst_f = single ? A.out + (long long)f * A.q.S * T
                         : A.partial + ((long long)split * A.F + f) * A.q.S * T;
@@ -314,7 +403,10 @@ __global__ void __launch_bounds__(kMaxThreads, 1) k_forward_batched(const BatchF
     local /= d.n_ttiles;
     const int st = (int)(local % d.n_stiles);
     const int f = (int)(local / d.n_stiles);
-    const int k0 = tt * A.t_tile;
+    const float *state_f0 = d.state + (long long)f * 5 * d.stride;
+    const int k0 = band_tile_start<false>(d.q, state_f0, d.stride, 0, d.n, A.s_tile, st, A.t_tile, tt,
+                                          reinterpret_cast<float *>(m.srec));
+    if (k0 < 0) continue;  // no arrival in this tile; the traces were zeroed
     const int klen = min(A.t_tile, d.q.T - k0);
     const bool ok = forward_item<false, G>(d.q, d.state + (long long)f * 5 * d.stride, d.stride, 0, d.n, A.s_tile,
                                            A.t_tile, A.nb_tile, st, k0, klen, d.out + (long long)f * d.q.S * d.q.T,
@@ -384,6 +476,7 @@ FwdKernel forward_kernel(bool uniform, int group) {
     case 1: return k_forward<false, 1>;
     case 2: return k_forward<false, 2>;
     case 4: return k_forward<false, 4>;
+    case 16: return k_forward<false, 16>;
     default: return k_forward<false, 8>;
   }
 }
@@ -406,11 +499,13 @@ int forward_default_s_tile(int t_tile, int nb_tile) {
 FwdPlan forward_plan(int S, int T, long long n, int F, int sms, int s_tile_o, int t_tile_o,
                      int nb_tile_o, int splits_o, int group_o) {
   FwdPlan p{};
-  p.group = (group_o == 1 || group_o == 2 || group_o == 4) ? group_o : 8;
-  // Default: up to 2048 samples per CTA, 512-ball TMA stages, and as many
-  // sensors (warps) as fit in 227 KB of shared memory with the compensated
-  // (high, low) trace tiles, at most 16: 12 x 2048 for 4096-sample traces.
-  int tt = t_tile_o > 0 ? t_tile_o : std::min(T, 2048);
+  p.group = (group_o == 1 || group_o == 2 || group_o == 4 || group_o == 16) ? group_o : 8;
+  // Default: up to kDefaultTTile samples per CTA, 512-ball TMA stages, and as
+  // many sensors (warps) as fit in 227 KB of shared memory with the
+  // compensated (high, low) trace tiles, at most 16: 16 x 1536.  More sensors
+  // per CTA share each ball's load and cull; with arrival-band tiles the
+  // shorter tiles cost little.
+  int tt = t_tile_o > 0 ? t_tile_o : std::min(T, kDefaultTTile);
   tt = std::min(std::min(tt, T), 16384);
   tt = (tt + 3) & ~3;
   p.t_tile = tt;
@@ -451,6 +546,14 @@ FwdPlan forward_plan(int S, int T, long long n, int F, int sms, int s_tile_o, in
 cudaError_t launch_forward(const FwdArgs &a, const FwdPlan &p, bool uniform, cudaStream_t st) {
   auto fn = forward_kernel(uniform, p.group);
   cudaError_t e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)p.smem);
+  if (e != cudaSuccess) return e;
+  // CTAs write only the sample band their balls reach: zero the rest first
+  const size_t frame_bytes = sizeof(float) * (size_t)a.F * a.q.S * a.q.T;
+  if (p.n_splits > 1) {
+    e = cudaMemsetAsync(a.partial, 0, frame_bytes * p.n_splits, st);
+  } else if (!(a.flags & PA_ACCUMULATE)) {
+    e = cudaMemsetAsync(a.out, 0, frame_bytes, st);
+  }
   if (e != cudaSuccess) return e;
   const long long grid = (long long)a.F * p.n_stiles * p.n_ttiles * p.n_splits;
   fn<<<(unsigned)grid, 32 * p.s_tile, p.smem, st>>>(a);

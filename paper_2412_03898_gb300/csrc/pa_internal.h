@@ -100,6 +100,8 @@ FwdPlan forward_plan(int S, int T, long long n, int F, int sms, int s_tile_overr
                      int t_tile_override, int nb_tile_override, int splits_override, int group_override);
 size_t forward_smem_bytes(int s_tile, int t_tile, int nb_tile);
 // Most sensors per CTA (<= 16) whose compensated trace tiles fit in 227 KB.
+// default samples per forward CTA (16 sensors x 1536 samples fill 227 KB)
+constexpr int kDefaultTTile = 1536;
 int forward_default_s_tile(int t_tile, int nb_tile);
 int forward_blocks_per_sm(const FwdPlan &p, bool uniform);
 
