@@ -7,12 +7,12 @@
 //  - One warp owns one ball (static mode: one (frame, ball) item) and loops
 //    over all sensors.  The 32 lanes compute the window, phase and gradient
 //    factors of 32 (ball, sensor) pairs in parallel and publish them,
-//    compacted, in shared memory; the warp then walks four pairs at a time,
-//    one per 8-lane sub-warp, each lane on two consecutive samples per step
-//    (a float2 residual load from L2, packed FP32x2 arithmetic, next step's
+//    compacted, in shared memory; the warp then walks eight pairs at a time,
+//    one per 4-lane sub-warp, each lane on four consecutive samples per step
+//    (a float4 residual load from L2, packed FP32x2 arithmetic, next step's
 //    load in flight), accumulating per lane
 //        S1 = sum g E u,  S3 = sum g E u^3,  SR = sum g E (1 - tau^2/a^2)
-//    which an 8-lane shuffle reduction turns into the pair's sums; the
+//    which a 4-lane shuffle reduction turns into the pair's sums; the
 //    sub-warp's first lane folds them with the pair's factors into its
 //    gradient accumulators.
 //  - A warp-shuffle reduction over lanes (i.e. over sensors and samples) at
@@ -45,6 +45,7 @@ __device__ __forceinline__ void ball_frame_grad(const Acq &q, const float *gfram
                                                 float4 *rec, int lane, float bx, float by, float bz, float a,
                                                 float p, float out[5], bool &dom) {
   const int S = q.S, T = q.T;
+  const float mbias = window_bias((q.kappa * K_S) * (q.kappa * K_S));
   float gx = 0.f, gy = 0.f, gz = 0.f, ga = 0.f, gp = 0.f;
   if (a > 0.f && p != 0.f) {
     for (int s0 = 0; s0 < S; s0 += 32) {
@@ -75,54 +76,59 @@ __device__ __forceinline__ void ball_frame_grad(const Acq &q, const float *gfram
         rec[3 * pos + 2] = r2;
       }
       __syncwarp();
-      // Four pairs at a time, one per 8-lane sub-warp: each sub-warp walks its
-      // pair's whole window, each lane two consecutive samples per step
-      // (one float2 load and packed FP32x2 arithmetic), the next step's load
-      // issued before the current step's arithmetic.
-      const int sub = lane >> 3, sl = lane & 7;
+      // Eight pairs at a time, one per 4-lane sub-warp: each sub-warp walks
+      // its pair's whole window, each lane four consecutive samples per step
+      // (one float4 residual load, two packed FP32x2 halves), the next step's
+      // load issued before the current step's arithmetic.  Samples of the
+      // aligned float4s outside the window get weight 0 from the window mask
+      // (u^2 <= (kappa K_S)^2, the forward's own test).
+      const int sub = lane >> 2, sl = lane & 3;
       const float2 negk = make_float2(-K_2LN2, -K_2LN2), one = make_float2(1.f, 1.f);
-      for (int g0 = 0; g0 < nv; g0 += 4) {
+      for (int g0 = 0; g0 < nv; g0 += 8) {
         const int i = g0 + sub;
         const bool act = i < nv;
         const int ii = act ? i : 0;
         const float4 a0 = rec[3 * ii + 0], a2 = rec[3 * ii + 2];
         const int klo = __float_as_int(a2.y);
         const int khi = act ? klo + __float_as_int(a2.z) - 1 : -1;
-        const int ka = klo & ~1;  // float2-aligned start (rows start 16-byte aligned, T % 4 == 0)
-        const float2 *row = reinterpret_cast<const float2 *>(gframe + (long long)__float_as_int(a2.w) * T);
+        // float4-aligned start: rows start 16-byte aligned (T % 4 == 0), and
+        // a float4 starting at k <= khi <= T - 1 ends at k + 3 <= T - 1
+        const int ka = klo & ~3;
+        const float4 *row = reinterpret_cast<const float4 *>(gframe + (long long)__float_as_int(a2.w) * T);
         const int nit = act ? ((khi - ka) >> 4) + 1 : 0;
         const int nmax = __reduce_max_sync(FULL, nit);
-        int kk = ka + 2 * sl;
-        float2 u2;
-        u2.x = fmaf((float)(kk - klo), -a0.y, a0.x);
-        u2.y = u2.x - a0.y;
-        const float2 nd2 = make_float2(-16.f * a0.y, -16.f * a0.y);
+        int kk = ka + 4 * sl;
+        const float du = a0.y;
+        float2 ua, ub;  // u at kk, kk + 1 and kk + 2, kk + 3
+        ua.x = fmaf((float)(kk - klo), -du, a0.x);
+        ua.y = ua.x - du;
+        ub.x = fmaf(-2.f, du, ua.x);
+        ub.y = fmaf(-3.f, du, ua.x);
+        const float2 nd2 = make_float2(-16.f * du, -16.f * du);
         float2 S1 = make_float2(0.f, 0.f), S3 = S1, SR = S1;
-        // residual at samples kk, kk+1 (zero outside [klo, khi]; kk <= khi
-        // implies kk + 1 <= T - 1 since kk is even and T - 1 odd)
-        auto fetch = [&](int k) {
-          float2 v = make_float2(0.f, 0.f);
-          if (k <= khi) v = __ldg(row + (k >> 1));
-          if (k < klo) v.x = 0.f;
-          if (k + 1 > khi) v.y = 0.f;
-          return v;
-        };
-        float2 gcur = fetch(kk);
-        for (int it = 0; it < nmax; ++it, kk += 16) {
-          const float2 gnext = fetch(kk + 16);
-          const float2 sq = __fmul2_rn(u2, u2);                         // u^2
-          const float2 E = make_float2(ex2(-sq.x), ex2(-sq.y));         // exp(-tau^2/(2a^2))
-          const float2 ge = __fmul2_rn(gcur, E);
+        auto half = [&](const float2 u2, const float2 g2) {
+          const float2 sq = __fmul2_rn(u2, u2);                                      // u^2
+          const float2 msk = make_float2(window_mask(sq.x, mbias), window_mask(sq.y, mbias));
+          const float2 E = make_float2(ex2(-sq.x), ex2(-sq.y));                      // exp(-tau^2/(2a^2))
+          const float2 ge = __fmul2_rn(__fmul2_rn(g2, msk), E);
           const float2 gu = __fmul2_rn(ge, u2);
-          S1 = __fadd2_rn(S1, gu);                                      // sum g E u
-          S3 = __ffma2_rn(gu, sq, S3);                                  // sum g E u^3
-          SR = __ffma2_rn(ge, __ffma2_rn(sq, negk, one), SR);           // sum g E (1 - tau^2/a^2)
-          u2 = __fadd2_rn(u2, nd2);
+          S1 = __fadd2_rn(S1, gu);                                                   // sum g E u
+          S3 = __ffma2_rn(gu, sq, S3);                                               // sum g E u^3
+          SR = __ffma2_rn(ge, __ffma2_rn(sq, negk, one), SR);                        // sum g E (1 - tau^2/a^2)
+        };
+        const float4 zero4 = make_float4(0.f, 0.f, 0.f, 0.f);
+        float4 gcur = kk <= khi ? __ldg(row + (kk >> 2)) : zero4;
+        for (int it = 0; it < nmax; ++it, kk += 16) {
+          const float4 gnext = kk + 16 <= khi ? __ldg(row + ((kk + 16) >> 2)) : zero4;
+          half(ua, make_float2(gcur.x, gcur.y));
+          half(ub, make_float2(gcur.z, gcur.w));
+          ua = __fadd2_rn(ua, nd2);
+          ub = __fadd2_rn(ub, nd2);
           gcur = gnext;
         }
         float s1 = S1.x + S1.y, s3 = S3.x + S3.y, sr = SR.x + SR.y;
 #pragma unroll
-        for (int o = 4; o > 0; o >>= 1) {
+        for (int o = 2; o > 0; o >>= 1) {
           s1 += __shfl_xor_sync(FULL, s1, o);
           s3 += __shfl_xor_sync(FULL, s3, o);
           sr += __shfl_xor_sync(FULL, sr, o);

@@ -300,7 +300,7 @@ int32_t pa_forward_batched(const pa_scene *scenes, int32_t n_scenes, uint32_t fl
   if (n_scenes < 0 || n_scenes > PA_MAX_SCENES || (n_scenes > 0 && scenes == nullptr)) return PA_ERR_INVALID_ARG;
   if ((flags & ~PA_ACCUMULATE) != 0) return PA_ERR_INVALID_ARG;
   if (tiles && (tiles[0] < 0 || tiles[0] > 16 || tiles[1] < 0 || (tiles[1] & 3) != 0 || tiles[2] < 0 ||
-                (tiles[2] & 3) != 0 || tiles[4] < 0 || tiles[4] > 8))
+                (tiles[2] & 3) != 0 || tiles[4] < 0 || tiles[4] > 16))
     return PA_ERR_INVALID_ARG;
   if (workspace == nullptr || workspace_bytes < pa_batched_workspace_size() || !aligned(workspace, 16))
     return PA_ERR_WORKSPACE;
@@ -321,7 +321,7 @@ int32_t pa_forward_batched(const pa_scene *scenes, int32_t n_scenes, uint32_t fl
   t_tile = std::min(std::min(t_tile, maxT), 16384);
   const int nb_tile = tiles && tiles[2] > 0 ? tiles[2] : 512;
   const int s_tile = tiles && tiles[0] > 0 ? tiles[0] : pa::forward_default_s_tile(t_tile, nb_tile);
-  const int group = tiles && tiles[4] == 4 ? 4 : 8;
+  const int group = tiles && (tiles[4] == 1 || tiles[4] == 2 || tiles[4] == 4 || tiles[4] == 16) ? tiles[4] : 8;
   const size_t smem = pa::forward_smem_bytes(s_tile, t_tile, nb_tile);
   if ((long long)smem > d->max_smem) return PA_ERR_INVALID_ARG;
   // scenes with balls, heaviest items (most balls) first

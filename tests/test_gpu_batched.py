@@ -35,8 +35,8 @@ def _states(sc):
     return sc.frames if sc.frames is not None else sc.balls[None]
 
 
-def test_forward_batched_equals_single_and_oracle(pa):
-    tiles = (12, 2048, 256, 1, 8)
+@pytest.mark.parametrize("tiles", [(12, 2048, 256, 1, 8), (16, 1536, 512, 1, 16), (7, 512, 128, 1, 2)])
+def test_forward_batched_equals_single_and_oracle(pa, tiles):
     scs = _scenes()
     batch = [pa.Scene(geometry(sc), dev_pad(_states(sc)), sc.n_balls) for sc in scs]
     pa.forward_batched(batch, tiles=tiles)
@@ -88,3 +88,16 @@ def test_adjoint_batched_equals_single_and_oracle(pa):
         got = b.grad_state[..., :sc.n_balls].cpu().numpy()
         for ch in range(5):
             assert rel_l2(got[:, ch], want[:, ch]) <= GRAD_TOL
+
+
+def test_tune_batched_accepts_every_default_candidate(pa):
+    from paper_2412_03898_gb300 import autotune
+    scs = _scenes()
+    batch = [pa.Scene(geometry(sc), dev_pad(_states(sc)), sc.n_balls) for sc in scs]
+    best = autotune.tune_batched(batch, reps=1)
+    assert tuple(best) in [tuple(c) for c in autotune.DEFAULT_CANDIDATES]
+    pa.forward_batched(batch, tiles=best)
+    pa.device_error()
+    for sc, b in zip(scs, batch):
+        y_o, _ = oracle.forward(_states(sc), sc.sensors, sc.c, sc.fs, sc.t0, sc.n_samples, sc.kappa)
+        assert rel_l2(b.traces.cpu().numpy(), y_o) <= TRACE_TOL
