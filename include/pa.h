@@ -152,6 +152,23 @@ PA_API int32_t pa_device_error(void *stream, int32_t *out);
 PA_API int32_t pa_deform_balls(const pa_canon *canon, const float *t_frames, int32_t n_frames,
                         float *state_out, void *stream);
 
+/* Chain rule of Eq. 1-2 (Sec. 2.2; the paper makes every (theta, sigma,
+ * omega) and the canonical attributes learnable) on its own: from per-frame
+ * state gradients
+ *   g_state   device [n_frames][5][canon->stride] = dL/d(state at t_f), e.g.
+ *             the static-mode pa_adjoint output for the states that
+ *             pa_deform_balls produced for the same t_frames,
+ * writes dL/d(canonical cloud) to grads->state [5][stride] and
+ * dL/d(omega, theta, sigma) to grads->omega / theta / sigma
+ * [5][n_basis][stride] (all device, caller-owned).  pa_deform_balls, the
+ * static pa_adjoint and this call give pa_adjoint's 4D mode up to float
+ * summation order, at the cost of two [n_frames][5][stride] buffers; the
+ * static adjoint runs at higher occupancy than the fused 4D kernel.
+ * flags: PA_ACCUMULATE adds to the outputs.  sigma_n <= 0 records
+ * PA_ERR_DOMAIN and that term gets zero gradient. */
+PA_API int32_t pa_deform_backward(const pa_canon *canon, const float *t_frames, int32_t n_frames,
+                                  const float *g_state, pa_grads *grads, uint32_t flags, void *stream);
+
 /* Scratch bytes pa_forward needs for this problem (0 if none). */
 PA_API size_t pa_forward_workspace_size(const pa_geom *geom, const pa_balls *balls, int32_t n_frames);
 

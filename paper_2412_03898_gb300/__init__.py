@@ -22,7 +22,7 @@ from . import _lib
 from ._lib import PAError
 
 __all__ = [
-    "PAError", "Geometry", "round4", "pad_last", "deform_balls", "forward", "adjoint", "residual_loss", "sumsq",
+    "PAError", "Geometry", "round4", "pad_last", "deform_balls", "deform_backward", "forward", "adjoint", "residual_loss", "sumsq",
     "count_contributions", "adam_step", "device_error", "forward_plan", "forward_workspace_size",
     "PAProject", "PAProject4D", "PALoss", "Scene", "forward_batched", "adjoint_batched", "adam_step_scheduled", "step_increment",
 ]
@@ -159,6 +159,28 @@ def deform_balls(canon: torch.Tensor, omega: torch.Tensor, theta: torch.Tensor, 
     _check(out, "out")
     _lib.check(_LIB.pa_deform_balls(ctypes.byref(cs), t_frames.data_ptr(), F, out.data_ptr(), _stream()),
                "pa_deform_balls")
+    return out
+
+
+def deform_backward(canon: torch.Tensor, omega: torch.Tensor, theta: torch.Tensor, sigma: torch.Tensor,
+                    t_frames: torch.Tensor, g_state: torch.Tensor, n: Optional[int] = None, out=None,
+                    accumulate: bool = False):
+    """Chain rule of Eq. 1-2: per-frame state gradients g_state [F, 5, stride]
+    -> (g_canon [5, stride], g_omega, g_theta, g_sigma [5, Nb, stride])."""
+    cs, n = _canon_struct(canon, omega, theta, sigma, n)
+    _check(t_frames, "t_frames")
+    _check(g_state, "g_state")
+    F = int(t_frames.numel())
+    if tuple(g_state.shape) != (F, 5, canon.shape[-1]):
+        raise ValueError(f"g_state must be [{F}, 5, {canon.shape[-1]}], got {tuple(g_state.shape)}")
+    if out is None:
+        out = (torch.empty_like(canon), torch.empty_like(omega), torch.empty_like(theta), torch.empty_like(sigma))
+    for o in out:
+        _check(o, "out")
+    grads = _lib.pa_grads(*[o.data_ptr() for o in out])
+    _lib.check(_LIB.pa_deform_backward(ctypes.byref(cs), t_frames.data_ptr(), F, g_state.data_ptr(),
+                                       ctypes.byref(grads), _lib.PA_ACCUMULATE if accumulate else 0, _stream()),
+               "pa_deform_backward")
     return out
 
 

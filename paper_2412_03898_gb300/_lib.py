@@ -79,6 +79,7 @@ def load() -> ctypes.CDLL:
         "pa_version": (i32, []),
         "pa_device_error": (i32, [P, I32P]),
         "pa_deform_balls": (i32, [C, P, i32, P, P]),
+        "pa_deform_backward": (i32, [C, P, i32, P, GR, u32, P]),
         "pa_forward_workspace_size": (sz, [G, B, i32]),
         "pa_forward_workspace_size_ex": (sz, [G, B, i32, I32P]),
         "pa_forward": (i32, [G, B, i32, P, u32, P, sz, P]),
@@ -120,7 +121,8 @@ def check(status: int, where: str) -> None:
 
 def exported_symbols() -> list[str]:
     """Names of the C-ABI entry points declared in this module."""
-    return ["pa_status_string", "pa_version", "pa_device_error", "pa_deform_balls", "pa_forward_workspace_size",
+    return ["pa_status_string", "pa_version", "pa_device_error", "pa_deform_balls", "pa_deform_backward",
+            "pa_forward_workspace_size",
             "pa_forward_workspace_size_ex", "pa_forward", "pa_forward_ex", "pa_forward_plan_info", "pa_adjoint",
             "pa_batched_workspace_size", "pa_forward_batched", "pa_adjoint_batched",
             "pa_loss_workspace_size", "pa_residual_loss", "pa_residual_loss_noalloc", "pa_sumsq", "pa_count_contributions", "pa_adam_step",

@@ -177,6 +177,23 @@ int32_t pa_deform_balls(const pa_canon *canon, const float *t_frames, int32_t n_
                                        static_cast<cudaStream_t>(stream)));
 }
 
+int32_t pa_deform_backward(const pa_canon *canon, const float *t_frames, int32_t n_frames, const float *g_state,
+                           pa_grads *grads, uint32_t flags, void *stream) {
+  int rc = check_canon(canon);
+  if (rc) return rc;
+  if (n_frames < 0 || (flags & ~PA_ACCUMULATE) != 0 || grads == nullptr) return PA_ERR_INVALID_ARG;
+  if (canon->n == 0) return PA_OK;
+  if (!grads->state || !grads->omega || !grads->theta || !grads->sigma) return PA_ERR_INVALID_ARG;
+  if (n_frames > 0 && (t_frames == nullptr || g_state == nullptr)) return PA_ERR_INVALID_ARG;
+  const DevInfo *d = dev_info();
+  if (!d) return PA_ERR_CUDA;
+  return cuda_status(pa::launch_deform_backward(canon->canon, canon->omega, canon->theta, canon->sigma, canon->n,
+                                                canon->stride, canon->n_basis, t_frames, n_frames, g_state,
+                                                grads->state, grads->omega, grads->theta, grads->sigma,
+                                                (flags & PA_ACCUMULATE) != 0, d->err,
+                                                static_cast<cudaStream_t>(stream)));
+}
+
 size_t pa_forward_workspace_size_ex(const pa_geom *geom, const pa_balls *balls, int32_t n_frames,
                                     const int32_t *tiles) {
   if (check_geom(geom) || check_balls(balls) || n_frames <= 0 || balls->n == 0) return 0;

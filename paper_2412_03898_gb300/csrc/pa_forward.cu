@@ -103,7 +103,6 @@ __device__ __forceinline__ bool forward_item(const Acq &q, const float *state_f,
   bool dom = false;
   // window bound in scaled units: |u| <= kappa K_S (Gaussian), |u| <= 1 (uniform)
   const float umax2 = UNIFORM ? 1.f : (q.kappa * K_S) * (q.kappa * K_S);
-  const float mbias = window_bias(umax2);
 
   for (int t = 0; t < ntiles; ++t) {
     const int stage = t & 1;
@@ -178,20 +177,24 @@ __device__ __forceinline__ bool forward_item(const Acq &q, const float *state_f,
           for (int base = kmin; base <= kmax; base += 32) {
             const int k = base + lane;
             if (k <= kmax) {
-              // the group's pulses at this sample, summed in registers: per
-              // ball pair one packed u^2, amp*u and mask product, then a
-              // packed FMA into one of two partial sums
-              float2 acc[2] = {make_float2(0.f, 0.f), make_float2(0.f, 0.f)};
+              // the group's pulses at this sample, summed in registers (one
+              // partial sum per ball pair keeps the dependency chains short)
+              float tp[(G + 1) / 2];
 #pragma unroll
               for (int h = 0; h < (G + 1) / 2; ++h) {
                 const float2 sq = __fmul2_rn(u2[h], u2[h]);
-                const float2 msk = make_float2(window_mask(sq.x, mbias), window_mask(sq.y, mbias));
-                const float2 wm = __fmul2_rn(__fmul2_rn(amp2[h], u2[h]), msk);
-                const float2 E = UNIFORM ? make_float2(1.f, 1.f) : make_float2(ex2(-sq.x), ex2(-sq.y));
-                acc[h & 1] = __ffma2_rn(wm, E, acc[h & 1]);
+                const float2 w = __fmul2_rn(amp2[h], u2[h]);
+                const float ex = UNIFORM ? 1.f : ex2(-sq.x);
+                const float ey = UNIFORM ? 1.f : ex2(-sq.y);
+                float th = sq.x <= umax2 ? w.x * ex : 0.f;
+                if (sq.y <= umax2) th = fmaf(w.y, ey, th);
+                tp[h] = th;
               }
-              const float2 a2 = __fadd2_rn(acc[0], acc[1]);
-              const float t = a2.x + a2.y;
+#pragma unroll
+              for (int st = 1; st < (G + 1) / 2; st *= 2)
+#pragma unroll
+                for (int h = 0; h + st < (G + 1) / 2; h += 2 * st) tp[h] += tp[h + st];
+              const float t = tp[0];
               // compensated accumulation: a sample collects the cancelling
               // pulses of thousands of balls, and a plain FP32 running sum
               // loses ~1e-5 relative by 1e5 balls.  Dekker's FastTwoSum is

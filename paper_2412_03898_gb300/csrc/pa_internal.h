@@ -112,6 +112,10 @@ cudaError_t launch_count(const Acq &q, const float *state, long long n, long lon
                          unsigned long long *out, cudaStream_t st);
 cudaError_t launch_adjoint_static(const AdjArgs &a, int sms, cudaStream_t st);
 cudaError_t launch_adjoint_4d(const AdjArgs &a, int sms, cudaStream_t st);
+cudaError_t launch_deform_backward(const float *canon, const float *omega, const float *theta, const float *sigma,
+                                   long long n, long long stride, int nb, const float *t, int F, const float *gstate,
+                                   float *g_canon, float *g_omega, float *g_theta, float *g_sigma, bool acc,
+                                   unsigned *err, cudaStream_t st);
 cudaError_t launch_deform(const float *canon, const float *omega, const float *theta,
                           const float *sigma, long long n, long long stride, int nb,
                           const float *t, int F, float *out, unsigned *err, cudaStream_t st);

@@ -56,6 +56,73 @@ __global__ void __launch_bounds__(256) k_deform(const float *__restrict__ canon,
   if (dom) set_error(err, PA_ERR_DOMAIN);
 }
 
+// Chain rule of Eq. 1-2 from per-frame state gradients g(f) = dL/dq(t_f) to
+// the canonical cloud and the deformation parameters.  One thread per
+// (channel, ball); basis functions in the outer loop, frames in the inner
+// one, so every output is written once (no read-modify-write).  With
+// d = (t_f - theta)/sigma and b = exp(-d^2/2):
+//   dL/domega = q0 sum_f g b
+//   dL/dtheta = q0 omega/sigma sum_f g b d
+//   dL/dsigma = q0 omega/sigma sum_f g b d^2
+//   dL/dq0    = sum_f g (1 + H(t_f)) = sum_f g + sum_n omega_n sum_f g b_n.
+// g(f) of a thread is re-read per basis function from L1 (one 128-byte line
+// per warp and frame).
+__global__ void __launch_bounds__(256) k_deform_backward(const float *__restrict__ canon,
+                                                         const float *__restrict__ omega,
+                                                         const float *__restrict__ theta,
+                                                         const float *__restrict__ sigma, long long n,
+                                                         long long stride, int nb, const float *__restrict__ t,
+                                                         int F, const float *__restrict__ gstate,
+                                                         float *__restrict__ g_canon, float *__restrict__ g_omega,
+                                                         float *__restrict__ g_theta, float *__restrict__ g_sigma,
+                                                         bool acc, unsigned *err) {
+  const float L2E_HALF = 0.72134752044448170368f;  // log2(e)/2
+  bool dom = false;
+  for (long long it = blockIdx.x * (long long)blockDim.x + threadIdx.x; it < 5 * n;
+       it += (long long)gridDim.x * blockDim.x) {
+    const int c = (int)(it / n);
+    const long long b = it - (long long)c * n;
+    const float q0 = __ldg(canon + (long long)c * stride + b);
+    const float *gq = gstate + (long long)c * stride + b;  // frame f at gq[f * 5 * stride]
+    float gsum = 0.f;
+    for (int f = 0; f < F; ++f) gsum += __ldg(gq + (long long)f * 5 * stride);
+    float gcan = gsum;
+    for (int k = 0; k < nb; ++k) {
+      const long long gi = ((long long)c * nb + k) * stride + b;
+      const float om = __ldg(omega + gi), th = __ldg(theta + gi), sg = __ldg(sigma + gi);
+      float s0 = 0.f, s1 = 0.f, s2 = 0.f;
+      float is = 0.f;
+      if (sg > 0.f) {
+        is = 1.f / sg;
+        for (int f = 0; f < F; ++f) {
+          const float g = __ldg(gq + (long long)f * 5 * stride);
+          const float d = (__ldg(t + f) - th) * is;
+          const float gb = g * ex2(-d * d * L2E_HALF);
+          s0 += gb;
+          s1 = fmaf(gb, d, s1);
+          s2 = fmaf(gb * d, d, s2);
+        }
+      } else {
+        dom = true;  // term skipped, as in the forward deformation
+      }
+      gcan = fmaf(om, s0, gcan);
+      const float qo = q0 * om * is;
+      float vo = q0 * s0, vt = qo * s1, vs = qo * s2;
+      if (acc) {
+        vo += g_omega[gi];
+        vt += g_theta[gi];
+        vs += g_sigma[gi];
+      }
+      g_omega[gi] = vo;
+      g_theta[gi] = vt;
+      g_sigma[gi] = vs;
+    }
+    float *dst = g_canon + (long long)c * stride + b;
+    *dst = acc ? *dst + gcan : gcan;
+  }
+  if (dom) set_error(err, PA_ERR_DOMAIN);
+}
+
 // Per-frame partial sums of squared residuals in FP64 (each float4 is summed
 // in fp32 then promoted), optional residual 2 scale (pred - meas).
 __global__ void __launch_bounds__(256) k_loss_partial(const float4 *__restrict__ pred, const float4 *__restrict__ meas,
@@ -176,6 +243,18 @@ cudaError_t launch_deform(const float *canon, const float *omega, const float *t
   if (total == 0) return cudaSuccess;
   const long long blocks = std::min<long long>((total + 255) / 256, 152LL * 32);
   k_deform<<<(unsigned)blocks, 256, 0, st>>>(canon, omega, theta, sigma, n, stride, nb, t, F, out, err);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_deform_backward(const float *canon, const float *omega, const float *theta, const float *sigma,
+                                   long long n, long long stride, int nb, const float *t, int F, const float *gstate,
+                                   float *g_canon, float *g_omega, float *g_theta, float *g_sigma, bool acc,
+                                   unsigned *err, cudaStream_t st) {
+  const long long total = 5 * n;
+  if (total == 0) return cudaSuccess;
+  const long long blocks = std::min<long long>((total + 255) / 256, 152LL * 32);
+  k_deform_backward<<<(unsigned)blocks, 256, 0, st>>>(canon, omega, theta, sigma, n, stride, nb, t, F, gstate,
+                                                      g_canon, g_omega, g_theta, g_sigma, acc, err);
   return cudaGetLastError();
 }
 

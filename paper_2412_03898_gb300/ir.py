@@ -2,9 +2,13 @@
 kernels (Sec. 2.2, Fig. 2 stage 2; hyper-parameters of Sec. 3.2).
 
 One IR iteration: deform every frame (Eq. 1-2) -> forward projection of all
-frames -> per-frame FP64 L2 loss and residual -> 4D adjoint (states
-recomputed in-kernel) -> Adam on each parameter group with the paper's
-learning rates and step decay (step_size 160, drop 0.1).  The optimiser type
+frames -> per-frame FP64 L2 loss and residual -> 4D adjoint -> Adam on each
+parameter group with the paper's learning rates and step decay (step_size
+160, drop 0.1).  The 4D adjoint is, by default, the static adjoint over the
+deformed states the forward already used followed by the chain rule of
+Eq. 1-2 (pa_deform_backward); fused=True uses the single fused 4D kernel
+instead, which needs no per-frame gradient buffer but runs at lower
+occupancy.  The optimiser type
 is not named in the paper; Adam is this library's reading.
 
 Two execution forms of the same iteration:
@@ -23,7 +27,8 @@ from typing import Optional
 
 import torch
 
-from . import Geometry, adam_step_scheduled, adjoint, deform_balls, forward, residual_loss, step_increment
+from . import (Geometry, adam_step_scheduled, adjoint, deform_backward, deform_balls, forward, residual_loss,
+               step_increment)
 
 # Sec. 3.2: initial learning rates and step decay.
 LR_COORD = 5e-7
@@ -42,7 +47,7 @@ class GGBallIR:
     omega, theta, sigma; t_frames: [F]; meas: [F, S, T]."""
 
     def __init__(self, geom: Geometry, canon: torch.Tensor, deform: torch.Tensor, t_frames: torch.Tensor,
-                 meas: torch.Tensor, n: Optional[int] = None):
+                 meas: torch.Tensor, n: Optional[int] = None, fused: bool = False):
         self.geom = geom
         self.canon = canon
         self.deform = deform
@@ -60,6 +65,8 @@ class GGBallIR:
         self.traces = torch.empty(self.F, geom.n_sensors, geom.n_samples, dtype=torch.float32, device=dev)
         self.resid = torch.empty_like(self.traces)
         self.loss = torch.empty(self.F, dtype=torch.float64, device=dev)
+        self.fused = fused
+        self.g_state = None if fused else torch.empty(self.F, 5, stride, dtype=torch.float32, device=dev)
         self.step_count = 0
         self.step_dev = torch.zeros(1, dtype=torch.int32, device=dev)
         self.graph: Optional[torch.cuda.CUDAGraph] = None
@@ -78,8 +85,16 @@ class GGBallIR:
         forward(self.geom, self.state, self.n, out=self.traces, workspace=self._fws)
         residual_loss(self.traces, self.meas, want_loss=True, want_resid=True, loss_out=self.loss,
                       resid_out=self.resid, workspace=self._lws)
-        adjoint(self.geom, self.resid, canon=self.canon, omega=self.deform[0], theta=self.deform[1],
-                sigma=self.deform[2], t_frames=self.t, n=self.n, out=self._grads_tuple())
+        self._adjoint_4d(self.resid, self.t, self.state, self.g_state, accumulate=False)
+
+    def _adjoint_4d(self, resid, t, state, g_state, accumulate):
+        if self.fused:
+            adjoint(self.geom, resid, canon=self.canon, omega=self.deform[0], theta=self.deform[1],
+                    sigma=self.deform[2], t_frames=t, n=self.n, out=self._grads_tuple(), accumulate=accumulate)
+        else:
+            adjoint(self.geom, resid, state=state, n=self.n, out=g_state)
+            deform_backward(self.canon, self.deform[0], self.deform[1], self.deform[2], t, g_state, self.n,
+                            out=self._grads_tuple(), accumulate=accumulate)
 
     def lr_scale(self) -> float:
         """Step decay of Sec. 3.2 for the iteration last taken (1-based t):
@@ -153,8 +168,8 @@ class GGBallIR:
             forward(self.geom, st, self.n, out=self.traces[f:f + 1], workspace=self._fws)
             residual_loss(self.traces[f:f + 1], self.meas[f:f + 1], want_loss=True, want_resid=True,
                           loss_out=self.loss[f:f + 1], resid_out=self.resid[f:f + 1], workspace=self._lws)
-            adjoint(self.geom, self.resid[f:f + 1], canon=self.canon, omega=self.deform[0], theta=self.deform[1],
-                    sigma=self.deform[2], t_frames=tf, n=self.n, out=self._grads_tuple(), accumulate=f > 0)
+            self._adjoint_4d(self.resid[f:f + 1], tf, st, None if self.fused else self.g_state[f:f + 1],
+                             accumulate=f > 0)
         self._adam()
         return self.loss
 
@@ -162,7 +177,8 @@ class GGBallIR:
         from . import forward_plan
         p = forward_plan(self.geom, self.state[:1] if per_frame else self.state, self.n)
         fwd = 1 + (1 if p["n_splits"] > 1 else 0)
-        core = 1 + fwd + 2 + 1  # deform, forward(+split reduce), loss partial+final, adjoint
+        adj = 1 if self.fused else 2  # fused 4D adjoint, or static adjoint + deform backward
+        core = 1 + fwd + 2 + adj  # deform, forward(+split reduce), loss partial+final, adjoint
         adam = 4  # step counter + three parameter groups
         return (core * self.F if per_frame else core) + adam
 

@@ -57,6 +57,20 @@ def test_per_frame_form_matches_batched(pa):
     torch.testing.assert_close(a.g_deform, b.g_deform, rtol=1e-4, atol=1e-6 * float(a.g_deform.abs().max()))
 
 
+@pytest.mark.parametrize("per_frame", [False, True])
+def test_fused_and_unfused_4d_adjoint_agree(pa, per_frame):
+    from paper_2412_03898_gb300.ir import GGBallIR
+    geom, canon, deform, t, meas, n = _problem(pa, seed=6)
+    a = GGBallIR(geom, canon.clone(), deform.clone(), t, meas, n, fused=False)
+    b = GGBallIR(geom, canon.clone(), deform.clone(), t, meas, n, fused=True)
+    for ir in (a, b):
+        ir.step_per_frame() if per_frame else ir.step()
+    torch.cuda.synchronize()
+    torch.testing.assert_close(a.loss, b.loss, rtol=0, atol=0)  # same forward
+    torch.testing.assert_close(a.g_canon, b.g_canon, rtol=1e-4, atol=1e-6 * float(a.g_canon.abs().max()))
+    torch.testing.assert_close(a.g_deform, b.g_deform, rtol=1e-4, atol=1e-6 * float(a.g_deform.abs().max()))
+
+
 def test_scheduled_adam_matches_torch_adam_with_step_decay(pa):
     torch.manual_seed(1)
     n = 1000
