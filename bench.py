@@ -43,6 +43,38 @@ SMS = 152
 FP32_LANES = 128
 SM_MAX_MHZ_NOMINAL = 2070.0
 
+# DRAM traffic per launch (ncu dram__bytes_read.sum + dram__bytes_write.sum)
+# of the static-100k step's kernels, recorded with the SHA-256 of the sources
+# the kernel was built from; a recorded figure is reported only while those
+# sources are unchanged.
+TRAFFIC_FILE = os.path.join(ROOT, "profiles", "traffic_static100k.json")
+KERNEL_SOURCES = {
+    "forward": ["pa_forward.cu", "pa_common.cuh", "pa_internal.h"],
+    "adjoint": ["pa_adjoint.cu", "pa_common.cuh", "pa_internal.h"],
+}
+
+
+def sources_sha256(kind: str) -> str:
+    import hashlib
+    h = hashlib.sha256()
+    for name in KERNEL_SOURCES[kind]:
+        with open(os.path.join(ROOT, "paper_2412_03898_gb300", "csrc", name), "rb") as fh:
+            h.update(fh.read())
+    return h.hexdigest()
+
+
+def recorded_traffic(kind: str):
+    """Bytes per launch of the `kind` kernel(s) from the recorded ncu capture,
+    or None when there is none or the sources changed since."""
+    try:
+        with open(TRAFFIC_FILE) as fh:
+            rec = json.load(fh)[kind]
+    except (OSError, ValueError, KeyError):
+        return None
+    if rec.get("sources_sha256") != sources_sha256(kind):
+        return None
+    return rec.get("bytes_per_step")
+
 
 def parse():
     ap = argparse.ArgumentParser()
@@ -328,9 +360,9 @@ def run_ours(args):
     adj_avg = statistics.mean(t_adj)
     peak_ops = SMS * FP32_LANES * SM_MAX_MHZ_NOMINAL * 1e6
     if fwd_avg >= adj_avg:
-        dom, ops, dur = "forward (k_forward + split reduce)", FWD_OPS, fwd_avg
+        dom, ops, dur, kind = "forward (k_forward + split reduce)", FWD_OPS, fwd_avg, "forward"
     else:
-        dom, ops, dur = "adjoint (k_adjoint_static)", ADJ_OPS, adj_avg
+        dom, ops, dur, kind = "adjoint (k_adjoint_static)", ADJ_OPS, adj_avg, "adjoint"
     achieved = C * ops / (dur * 1e-3)
     launches_per_step = 1 + (1 if plan["n_splits"] > 1 else 0) + 2 + 1
     line = {
@@ -347,7 +379,7 @@ def run_ours(args):
                 "d2h_bytes_per_step": e2e_out},
         "gpu_launches": launches_per_step * args.steps,
         "roofline": {"bound": "alu", "kernel": dom, "achieved": achieved / 1e12, "peak": peak_ops / 1e12,
-                     "unit": "TFLOP/s", "frac": achieved / peak_ops, "traffic": None,
+                     "unit": "TFLOP/s", "frac": achieved / peak_ops, "traffic": recorded_traffic(kind),
                      "note": f"FP32 operations (FMA = 1) per contribution: forward {FWD_OPS}, adjoint {ADJ_OPS}; "
                              f"peak = {SMS} SMs x {FP32_LANES} FP32 lanes x {SM_MAX_MHZ_NOMINAL:.0f} MHz"},
         "kernels_ms": {"forward": fwd_avg, "loss": statistics.mean(t_loss), "adjoint": adj_avg},
