@@ -24,6 +24,7 @@ import numpy as np
 
 _HERE = os.path.dirname(os.path.abspath(__file__))
 _SRC = os.path.join(_HERE, "pa_oracle.c")
+_SRCS = [_SRC, os.path.join(_HERE, "pa_oracle_image.c")]
 _LIB = os.path.join(_HERE, "liboracle.so")
 _lock = threading.Lock()
 _lib = None
@@ -38,12 +39,13 @@ class OracleError(RuntimeError):
 
 
 def build(force: bool = False) -> str:
-    """Compile pa_oracle.c into liboracle.so (IEEE double, no fast-math)."""
-    if not force and os.path.exists(_LIB) and os.path.getmtime(_LIB) >= os.path.getmtime(_SRC):
+    """Compile pa_oracle.c and pa_oracle_image.c into liboracle.so (IEEE
+    double, no fast-math)."""
+    if not force and os.path.exists(_LIB) and all(os.path.getmtime(_LIB) >= os.path.getmtime(f) for f in _SRCS):
         return _LIB
     tmp = f"{_LIB}.{os.getpid()}.tmp"
     cmd = ["gcc", "-O2", "-fno-fast-math", "-ffp-contract=off", "-fopenmp", "-fPIC", "-shared",
-           "-o", tmp, _SRC, "-lm"]
+           "-o", tmp, *_SRCS, "-lm"]
     subprocess.run(cmd, check=True)
     os.replace(tmp, _LIB)
     return _LIB
@@ -74,6 +76,14 @@ def _load():
             lib.oracle_adjoint_4d.restype = i32
             lib.oracle_adjoint_4d.argtypes = [i64, i32, P, P, P, P, i32, P, i32, P, d, d, d, i32, d,
                                               P, P, P, P, P, i32]
+            lib.oracle_ubp_filter.restype = i32
+            lib.oracle_ubp_filter.argtypes = [i32, i32, d, d, P, P]
+            lib.oracle_ubp.restype = i32
+            lib.oracle_ubp.argtypes = [i32, i32, P, P, d, d, d, P, P, d, i32, i32, i32, P, i32]
+            lib.oracle_splat.restype = i32
+            lib.oracle_splat.argtypes = [i64, P, d, P, d, i32, i32, i32, P, i32]
+            lib.oracle_ssim.restype = i32
+            lib.oracle_ssim.argtypes = [i32, i32, P, P, d, P, P]
             _lib = lib
     return _lib
 
@@ -185,3 +195,65 @@ def adjoint_4d(canon, omega, theta, sigma, t, sensors, c, fs, t0, n_samples, kap
     if rc:
         raise OracleError(f"oracle_adjoint_4d failed ({rc})")
     return gc, go, gt, gs
+
+
+# ---------------------------------------------------------------------------
+# Imaging side (pa_oracle_image.c): UBP comparison reconstruction, point
+# cloud -> voxels, maximum amplitude projections and SSIM (Sec. 3.1-3.2).
+
+def ubp_filter(traces, fs, t0):
+    """b = 2 p - 2 t dp/dt per sensor trace; traces [..., S, T] -> same shape."""
+    p = _d(traces)
+    shp = p.shape
+    T = shp[-1]
+    p2 = p.reshape(-1, T)
+    b = np.zeros_like(p2)
+    rc = _load().oracle_ubp_filter(p2.shape[0], T, float(fs), float(t0), _p(p2), _p(b))
+    if rc != 0:
+        raise OracleError(f"oracle_ubp_filter: {rc}")
+    return b.reshape(shp)
+
+
+def ubp(b, sensors, center, c, fs, t0, origin, h, shape, nthreads=0):
+    """Back-projection of filtered traces b [S, T] onto a grid of shape
+    (nz, ny, nx) -> volume [nz, ny, nx]."""
+    b, sensors, center, origin = map(_d, (b, sensors, center, origin))
+    ns, T = b.shape
+    nz, ny, nx = shape
+    vol = np.zeros((nz, ny, nx))
+    rc = _load().oracle_ubp(ns, T, _p(sensors), _p(center), float(c), float(fs), float(t0), _p(b), _p(origin),
+                            float(h), nx, ny, nz, _p(vol), int(nthreads))
+    if rc != 0:
+        raise OracleError(f"oracle_ubp: {rc}")
+    return vol
+
+
+def splat(state, kappa, origin, h, shape, nthreads=0):
+    """Truncated Gaussian-ball pressure sum on a grid: state [5, N] -> [nz, ny, nx]."""
+    state, origin = _d(state), _d(origin)
+    n = state.shape[1]
+    nz, ny, nx = shape
+    vol = np.zeros((nz, ny, nx))
+    rc = _load().oracle_splat(n, _p(state), float(kappa), _p(origin), float(h), nx, ny, nz, _p(vol), int(nthreads))
+    if rc != 0:
+        raise OracleError(f"oracle_splat: {rc}")
+    return vol
+
+
+def maps(vol):
+    """Maximum amplitude projections of a volume [nz, ny, nx]: (XY = max over
+    z [ny, nx], YZ = max over x [nz, ny], XZ = max over y [nz, nx])."""
+    v = np.asarray(vol, dtype=np.float64)
+    return v.max(axis=0), v.max(axis=2), v.max(axis=1)
+
+
+def ssim(x, y, L=1.0, want_map=False):
+    """Mean SSIM of two images [H, W] (and the map over valid positions)."""
+    x, y = _d(x), _d(y)
+    H, W = x.shape
+    m = np.zeros((H - 10, W - 10))
+    out = np.zeros(1)
+    rc = _load().oracle_ssim(H, W, _p(x), _p(y), float(L), _p(m), _p(out))
+    if rc != 0:
+        raise OracleError(f"oracle_ssim: {rc}")
+    return (float(out[0]), m) if want_map else float(out[0])
