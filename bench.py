@@ -88,6 +88,7 @@ def parse():
     ap.add_argument("--no-batched", action="store_true", help="skip the 16-scene batched comparison")
     ap.add_argument("--steps-batched", type=int, default=2)
     ap.add_argument("--no-autotune", action="store_true")
+    ap.add_argument("--no-imaging", action="store_true", help="skip the UBP / splat / MAP / SSIM leg")
     a = ap.parse_args()
     a.warmup = max(a.warmup, 3)
     return a
@@ -354,6 +355,9 @@ def run_ours(args):
     batched = None
     if not args.no_batched:
         batched = bench_batched(args, pa, pa_inputs, dev, flush)
+    imaging = None
+    if not args.no_imaging:
+        imaging = bench_imaging(args, pa, pa_inputs, dev, flush)
     clocks = sampler.stop()
 
     fwd_avg = statistics.mean(t_fwd)
@@ -389,6 +393,8 @@ def run_ours(args):
         line["ir4d"] = ir4d
     if batched is not None:
         line["batched"] = batched
+    if imaging is not None:
+        line["imaging"] = imaging
     if rank == 0 and world == 1 and not args.no_cpu:
         line["cpu_baseline"] = cpu_baseline(sc)
     if rank == 0:
@@ -442,6 +448,61 @@ def bench_4d(args, pa, pa_inputs, dev, flush):
         del ir
     out["speedup_batched_vs_per_frame"] = res["batched_graph"] / res["per_frame"]
     out["contrib_per_s_batched"] = 2 * C * res["batched_graph"]
+    return out
+
+
+# Algorithmic FP32 operations per UBP (voxel, sensor) pair: r - r_s (3),
+# |r - r_s|^2 (3), n . (r - r_s) (3), d and cos/d^2 (4), fractional sample (1),
+# interpolation (2), weighted sums (2) = 18 (+1 rsqrt on the SFU).
+UBP_OPS = 18
+
+
+def bench_imaging(args, pa, pa_inputs, dev, flush):
+    """Imaging on the simulated heart (Sec. 3.1: 72,006 balls, 1,024 sensors on
+    a full 60 mm Fibonacci sphere, 4,096 samples): UBP of frame 0 onto 256^3
+    voxels of 0.2 mm over the (-25.6, 25.6) mm cube, the ball cloud splatted
+    onto the same grid, the XY / YZ / XZ MAPs of both and their SSIMs."""
+    import torch
+    sc = pa_inputs.heart_phantom()
+    n = sc.n_balls
+    st = pa.pad_last(torch.from_numpy(sc.frames[0]).to(dev)).contiguous()
+    geom = pa.Geometry(torch.from_numpy(sc.sensors).to(dev), sc.c, sc.fs, sc.t0, sc.n_samples, sc.kappa)
+    y = pa.forward(geom, st[None], n)[0].contiguous()
+    nvox = 256
+    grid = pa.Grid.cube(25.6, nvox)
+    b = torch.empty_like(y)
+    vol = torch.empty(grid.shape, dtype=torch.float32, device=dev)
+    gt = torch.empty_like(vol)
+
+    def timed(fn, reps):
+        fn()
+        torch.cuda.synchronize()
+        ms = []
+        for _ in range(reps):
+            flush.zero_()
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record()
+            fn()
+            e1.record()
+            e1.synchronize()
+            ms.append(e0.elapsed_time(e1))
+        return statistics.median(ms)
+
+    out = {"workload": f"heart-sim1 frame 0: {n} balls, {geom.n_sensors} sensors (60 mm sphere), "
+                       f"{geom.n_samples} samples; grid {nvox}^3 x {grid.h:.2f} mm"}
+    out["ubp_filter_ms"] = timed(lambda: pa.ubp_filter(y, sc.fs, sc.t0, out=b), 5)
+    ubp_ms = timed(lambda: pa.ubp(geom, b, grid, out=vol), 3)
+    pairs = geom.n_sensors * nvox ** 3
+    out["ubp_ms"] = ubp_ms
+    out["ubp_voxel_sensor_pairs_per_s"] = pairs / (ubp_ms * 1e-3)
+    peak = SMS * FP32_LANES * SM_MAX_MHZ_NOMINAL * 1e6
+    out["ubp_alu_frac"] = pairs * UBP_OPS / (ubp_ms * 1e-3) / peak
+    out["splat_ms"] = timed(lambda: pa.splat(st, grid, sc.kappa, n, out=gt), 3)
+    out["maps_ms"] = timed(lambda: pa.maps(vol, grid), 5)
+    mu, mg = pa.maps(vol, grid), pa.maps(gt, grid)
+    out["ssim_ms"] = timed(lambda: [pa.ssim(u, g, minmax=True) for u, g in zip(mu, mg)], 5)
+    out["ubp_vs_gt_map_ssim"] = {k: float(pa.ssim(u, g, minmax=True)) for k, u, g in zip(("xy", "yz", "xz"), mu, mg)}
+    pa.device_error()
     return out
 
 

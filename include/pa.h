@@ -65,6 +65,8 @@ extern "C" {
 
 /* Flags. */
 #define PA_ACCUMULATE 1u      /* add into the output instead of overwriting it */
+#define PA_SSIM_MINMAX 4u     /* pa_ssim only: scale each image to [0, 1] by its own minimum and
+                                 maximum first (a constant image becomes 0), L = 1 */
 #define PA_PROFILE_UNIFORM 2u /* pa_forward only: uniform ball of radius a (N-pulse
                                  p tau/(2R) on |tau| <= a), used for analytic tests */
 
@@ -130,6 +132,14 @@ typedef struct pa_scene {
 
 /* Most scenes one batched call takes. */
 #define PA_MAX_SCENES 64
+
+/* A voxel grid [nz][ny][nx] (x fastest); voxel (ix, iy, iz) is centred at
+ * origin + h (ix, iy, iz), in mm.  h > 0; nx, ny, nz >= 1. */
+typedef struct pa_grid {
+    float origin[3];
+    float h;
+    int32_t nx, ny, nz;
+} pa_grid;
 
 /* Human-readable name of a status code (static storage). */
 PA_API const char *pa_status_string(int32_t status);
@@ -306,6 +316,63 @@ PA_API int32_t pa_adam_step_scheduled(float *x, const float *g, float *m, float 
 
 /* Adds 1 to the device int32 *step (one-thread kernel, stream ordered). */
 PA_API int32_t pa_step_increment(int32_t *step, void *stream);
+
+/* ------------------------------------------------------------------------
+ * Imaging (Sec. 3.1-3.2, Tab. 1).  The paper compares 4D SlingBAG with the
+ * universal back-projection (UBP), shows maximum amplitude projections (MAPs)
+ * of reconstructions converted to voxel grids, and scores them by SSIM; it
+ * prints none of these methods, so each call below computes the textbook
+ * definition stated with it.
+ * ---------------------------------------------------------------------- */
+
+/* UBP filtering step (Xu and Wang): for every trace p(t_k), t_k = t0 + k/fs,
+ *   b(t_k) = 2 p(t_k) - 2 t_k dp/dt(t_k),
+ * dp/dt by central differences (one-sided at k = 0 and k = T-1).
+ * traces, b: device [n_traces][n_samples] (may not alias); n_samples >= 2. */
+PA_API int32_t pa_ubp_filter(const float *traces, int64_t n_traces, int32_t n_samples, float fs, float t0,
+                             float *b, void *stream);
+
+/* UBP back-projection of filtered traces b (device [n_sensors][n_samples],
+ * from pa_ubp_filter) onto `grid`:
+ *   vol(r) = sum_s w_s b_s(|r - r_s| / c) / sum_s w_s,
+ * w_s = cos(theta_s) / |r - r_s|^2, theta_s the angle between r - r_s and the
+ * sensor's inward normal (from r_s towards `center`, host float[3]); sensors
+ * with cos(theta_s) <= 0 are left out; b_s is linearly interpolated at the
+ * fractional sample (d/c - t0) fs and is 0 outside [0, T-1].  A voxel no
+ * sensor faces gets 0.  geom: sensors, c, fs, t0, n_samples (kappa unused).
+ * vol: device [nz][ny][nx], overwritten. */
+PA_API int32_t pa_ubp(const pa_geom *geom, const float *center, const float *b, const pa_grid *grid, float *vol,
+                      void *stream);
+
+/* Ball cloud -> voxel grid (SlingBAG's conversion of its point cloud,
+ * Sec. 2.1): vol(r) = sum_b p_b exp(-|r - mu_b|^2 / (2 a_b^2)) over the
+ * closed support |r - mu_b| <= kappa a_b (kappa > 0); balls with a <= 0 or
+ * p == 0 add nothing.  balls: one frame, device [5][stride]; vol: device
+ * [nz][ny][nx], overwritten.  Deterministic: every voxel sums its balls in
+ * index order. */
+PA_API int32_t pa_splat(const pa_balls *balls, float kappa, const pa_grid *grid, float *vol, void *stream);
+
+/* Maximum amplitude projections of vol (device [nz][ny][nx]): xy [ny][nx]
+ * (max over z), yz [nz][ny] (max over x), xz [nz][nx] (max over y); any of
+ * the three outputs may be NULL. */
+PA_API int32_t pa_map(const float *vol, const pa_grid *grid, float *xy, float *yz, float *xz, void *stream);
+
+/* Workspace bytes pa_ssim needs for H x W images. */
+PA_API size_t pa_ssim_workspace_size(int32_t H, int32_t W);
+
+/* Structural similarity (Wang, Bovik, Sheikh, Simoncelli 2004) of images x
+ * and y (device [H][W], H, W >= 11): local means, variances and covariance
+ * under an 11 x 11 Gaussian window (sigma 1.5, weights summing to 1) at every
+ * position where the window fits,
+ *   SSIM = (2 mx my + C1)(2 sxy + C2) / ((mx^2 + my^2 + C1)(sx^2 + sy^2 + C2)),
+ * C1 = (0.01 L)^2, C2 = (0.03 L)^2 (L > 0, the dynamic range).  With
+ * flags = PA_SSIM_MINMAX each image is first mapped to [0, 1] by its own
+ * minimum and maximum (reconstructions in arbitrary units against a ground
+ * truth) and L = 1.  Writes the mean to *mean (device double) and, if
+ * map != NULL, the SSIM map (device [(H-10)][(W-10)]).  workspace: device,
+ * pa_ssim_workspace_size bytes, 16-byte aligned. */
+PA_API int32_t pa_ssim(const float *x, const float *y, int32_t H, int32_t W, float L, uint32_t flags, float *map,
+                       double *mean, void *workspace, size_t workspace_bytes, void *stream);
 
 #ifdef __cplusplus
 }

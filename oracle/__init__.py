@@ -247,9 +247,20 @@ def maps(vol):
     return v.max(axis=0), v.max(axis=2), v.max(axis=1)
 
 
-def ssim(x, y, L=1.0, want_map=False):
-    """Mean SSIM of two images [H, W] (and the map over valid positions)."""
+def minmax01(x):
+    """Scale an image to [0, 1] by its own minimum and maximum (a constant
+    image becomes 0)."""
+    x = _d(x)
+    lo, hi = x.min(), x.max()
+    return (x - lo) / (hi - lo) if hi > lo else np.zeros_like(x)
+
+
+def ssim(x, y, L=1.0, want_map=False, minmax=False):
+    """Mean SSIM of two images [H, W] (and the map over valid positions);
+    minmax=True compares the [0, 1]-scaled images with L = 1."""
     x, y = _d(x), _d(y)
+    if minmax:
+        x, y, L = minmax01(x), minmax01(y), 1.0
     H, W = x.shape
     m = np.zeros((H - 10, W - 10))
     out = np.zeros(1)

@@ -302,3 +302,51 @@ def small_scene(seed: int, n_balls: int, n_sensors: int, n_samples: int,
     frames = gt_motion_frames(balls, axis, n_frames) if n_frames > 1 else None
     return Scene(f"small-{seed}", balls, fibonacci_hemisphere(n_sensors, radius), 1.5, 40.0, t0,
                  n_samples, kappa, n_frames, frames, axis)
+
+
+def heart_phantom(n_frames: int = 17, spacing: float = 0.4, a: float = 0.25, seed: int = 7) -> Scene:
+    """The "simulated heart" of the paper's first simulation (Sec. 3.1), built
+    from Gaussian balls: three mutually perpendicular rectangular slabs of
+    uniform pressure (stationary) and a Gaussian ellipsoid at the centre whose
+    pressure and size pulse over the frames, inside the cube (-25.6, 25.6) mm^3,
+    seen by 1,024 sensors on a full Fibonacci sphere of radius 60 mm.  The
+    paper gives no dimensions for the slabs or the ellipsoid; these are chosen
+    to fill the cube's centre: slabs 30 x 8 x 2 mm along x, y and z, ellipsoid
+    semi-axes (6, 4.5, 3.5) mm scaled by 1 + 0.15 sin(2 pi f / F) with peak
+    pressure 1 + 0.3 sin(2 pi f / F).
+
+    Slab balls sit on a jittered lattice of the given spacing (same every
+    frame); ellipsoid balls on a lattice whose positions scale with the
+    ellipsoid and whose pressure follows the Gaussian profile
+    exp(-r_e^2 / 2), r_e the ellipsoidal radius in units of the semi-axes,
+    kept out to r_e <= 2.  Returns a Scene whose `frames` holds the F states
+    (the ball count is the same in every frame)."""
+    rng = np.random.default_rng(seed)
+
+    def lattice(ext):
+        axes = [np.arange(-e / 2 + spacing / 2, e / 2, spacing) for e in ext]
+        g = np.stack(np.meshgrid(*axes, indexing="ij")).reshape(3, -1)
+        return g + rng.uniform(-0.1 * spacing, 0.1 * spacing, g.shape)
+
+    slabs = []
+    for ext in ((30.0, 8.0, 2.0), (2.0, 30.0, 8.0), (8.0, 2.0, 30.0)):
+        slabs.append(lattice(ext))
+    slab_pos = np.concatenate(slabs, axis=1)
+    semi = np.array([6.0, 4.5, 3.5])
+    unit = lattice(tuple(4.0 * semi)) / semi[:, None]  # in units of the semi-axes
+    re2 = (unit ** 2).sum(0)
+    unit = unit[:, re2 <= 4.0]
+    re2 = re2[re2 <= 4.0]
+    n_slab, n_ell = slab_pos.shape[1], unit.shape[1]
+    frames = np.empty((n_frames, 5, n_slab + n_ell), dtype=np.float32)
+    for f in range(n_frames):
+        ph = math.sin(2.0 * math.pi * f / n_frames)
+        scale, peak = 1.0 + 0.15 * ph, 1.0 + 0.3 * ph
+        frames[f, :3, :n_slab] = slab_pos
+        frames[f, 3, :n_slab] = a
+        frames[f, 4, :n_slab] = 0.6
+        frames[f, :3, n_slab:] = unit * semi[:, None] * scale
+        frames[f, 3, n_slab:] = a * scale
+        frames[f, 4, n_slab:] = peak * np.exp(-re2 / 2.0)
+    sensors = fibonacci_sphere(1024, 60.0)
+    return Scene("heart-sim1", frames[0].copy(), sensors, 1.5, 40.0, 0.0, 4096, 5.0, n_frames, frames, None)

@@ -25,6 +25,7 @@ __all__ = [
     "PAError", "Geometry", "round4", "pad_last", "deform_balls", "deform_backward", "forward", "adjoint", "residual_loss", "sumsq",
     "count_contributions", "adam_step", "device_error", "forward_plan", "forward_workspace_size",
     "PAProject", "PAProject4D", "PALoss", "Scene", "forward_batched", "adjoint_batched", "adam_step_scheduled", "step_increment",
+    "Grid", "ubp_filter", "ubp", "splat", "maps", "ssim",
 ]
 
 
@@ -455,3 +456,102 @@ class PALoss(torch.autograd.Function):
         _, resid = residual_loss(pred, meas, frame_scale=scale, want_loss=False, want_resid=True)
         gm = -resid if ctx.needs_input_grad[1] else None
         return resid, gm
+
+
+# ---------------------------------------------------------------------------
+# Imaging (Sec. 3.1-3.2, Tab. 1): UBP comparison reconstruction, ball cloud
+# -> voxels, maximum amplitude projections and SSIM.
+
+class Grid:
+    """Voxel grid [nz, ny, nx]; voxel (ix, iy, iz) centred at origin + h (ix, iy, iz) (mm)."""
+
+    def __init__(self, origin, h: float, shape):
+        self.origin = tuple(float(v) for v in origin)
+        self.h = float(h)
+        self.shape = tuple(int(v) for v in shape)  # (nz, ny, nx)
+        nz, ny, nx = self.shape
+        self._struct = _lib.pa_grid((ctypes.c_float * 3)(*self.origin), self.h, nx, ny, nz)
+
+    @classmethod
+    def cube(cls, half_width: float, n: int, center=(0.0, 0.0, 0.0)) -> "Grid":
+        """n^3 voxels filling the cube center +- half_width."""
+        h = 2.0 * half_width / n
+        origin = [c - half_width + 0.5 * h for c in center]
+        return cls(origin, h, (n, n, n))
+
+    def struct(self):
+        return self._struct
+
+
+def ubp_filter(traces: torch.Tensor, fs: float, t0: float, out: Optional[torch.Tensor] = None) -> torch.Tensor:
+    """UBP filtering b = 2p - 2t dp/dt along the last axis of traces [..., T]."""
+    _check(traces, "traces")
+    T = int(traces.shape[-1])
+    if out is None:
+        out = torch.empty_like(traces)
+    _check(out, "out")
+    _lib.check(_LIB.pa_ubp_filter(traces.data_ptr(), int(traces.numel() // T), T, float(fs), float(t0),
+                                  out.data_ptr(), _stream()), "pa_ubp_filter")
+    return out
+
+
+def ubp(geom: Geometry, b: torch.Tensor, grid: Grid, center=(0.0, 0.0, 0.0),
+        out: Optional[torch.Tensor] = None) -> torch.Tensor:
+    """UBP back-projection of filtered traces b [S, T] onto grid -> [nz, ny, nx]."""
+    _check(b, "b")
+    if tuple(b.shape) != (geom.n_sensors, geom.n_samples):
+        raise ValueError(f"b must be [{geom.n_sensors}, {geom.n_samples}], got {tuple(b.shape)}")
+    if out is None:
+        out = torch.empty(grid.shape, dtype=torch.float32, device=b.device)
+    _check(out, "out")
+    c = (ctypes.c_float * 3)(*[float(v) for v in center])
+    _lib.check(_LIB.pa_ubp(ctypes.byref(geom.struct()), c, b.data_ptr(), ctypes.byref(grid.struct()),
+                           out.data_ptr(), _stream()), "pa_ubp")
+    return out
+
+
+def splat(state: torch.Tensor, grid: Grid, kappa: float = 5.0, n: Optional[int] = None,
+          out: Optional[torch.Tensor] = None) -> torch.Tensor:
+    """Ball cloud [5, stride] (one frame) -> voxel grid [nz, ny, nx]."""
+    state, bs, n = _balls_struct(state, n)
+    if out is None:
+        out = torch.empty(grid.shape, dtype=torch.float32, device=state.device)
+    _check(out, "out")
+    _lib.check(_LIB.pa_splat(ctypes.byref(bs), float(kappa), ctypes.byref(grid.struct()), out.data_ptr(),
+                             _stream()), "pa_splat")
+    return out
+
+
+def maps(vol: torch.Tensor, grid: Grid):
+    """Maximum amplitude projections of vol [nz, ny, nx]: (xy [ny, nx], yz [nz, ny], xz [nz, nx])."""
+    _check(vol, "vol")
+    nz, ny, nx = grid.shape
+    if tuple(vol.shape) != (nz, ny, nx):
+        raise ValueError(f"vol must be {grid.shape}, got {tuple(vol.shape)}")
+    xy = torch.empty(ny, nx, dtype=torch.float32, device=vol.device)
+    yz = torch.empty(nz, ny, dtype=torch.float32, device=vol.device)
+    xz = torch.empty(nz, nx, dtype=torch.float32, device=vol.device)
+    _lib.check(_LIB.pa_map(vol.data_ptr(), ctypes.byref(grid.struct()), xy.data_ptr(), yz.data_ptr(),
+                           xz.data_ptr(), _stream()), "pa_map")
+    return xy, yz, xz
+
+
+def ssim(x: torch.Tensor, y: torch.Tensor, L: float = 1.0, want_map: bool = False,
+         workspace: Optional[torch.Tensor] = None, minmax: bool = False):
+    """Mean SSIM of images x, y [H, W] as a device float64 scalar (and the
+    map).  minmax=True scales each image to [0, 1] by its own minimum and
+    maximum first (L = 1)."""
+    _check(x, "x")
+    _check(y, "y")
+    if x.shape != y.shape or x.dim() != 2:
+        raise ValueError("x and y must be equal-shape 2D images")
+    H, W = int(x.shape[0]), int(x.shape[1])
+    need = int(_LIB.pa_ssim_workspace_size(H, W))
+    if workspace is None or workspace.numel() < need:
+        workspace = torch.empty(max(need, 16), dtype=torch.uint8, device=x.device)
+    mean = torch.empty((), dtype=torch.float64, device=x.device)
+    m = torch.empty(max(H - 10, 0), max(W - 10, 0), dtype=torch.float32, device=x.device) if want_map else None
+    _lib.check(_LIB.pa_ssim(x.data_ptr(), y.data_ptr(), H, W, float(L), _lib.PA_SSIM_MINMAX if minmax else 0,
+                            _ptr(m), mean.data_ptr(),
+                            workspace.data_ptr(), workspace.numel(), _stream()), "pa_ssim")
+    return (mean, m) if want_map else mean

@@ -18,6 +18,7 @@ PA_ERR_CUDA = 3
 PA_ERR_TIMEOUT = 4
 PA_ERR_WORKSPACE = 5
 PA_ACCUMULATE = 1
+PA_SSIM_MINMAX = 4
 PA_PROFILE_UNIFORM = 2
 
 c_float_p = ctypes.c_void_p  # device pointers travel as void*
@@ -50,6 +51,11 @@ class pa_scene(ctypes.Structure):
 
 
 PA_MAX_SCENES = 64
+
+
+class pa_grid(ctypes.Structure):
+    _fields_ = [("origin", ctypes.c_float * 3), ("h", ctypes.c_float), ("nx", ctypes.c_int32), ("ny", ctypes.c_int32),
+                ("nz", ctypes.c_int32)]
 
 
 class PAError(RuntimeError):
@@ -98,6 +104,12 @@ def load() -> ctypes.CDLL:
         "pa_adam_step_scheduled": (i32, [P, P, P, P, i64, ctypes.c_double, ctypes.c_double, ctypes.c_double,
                                          ctypes.c_double, i32, ctypes.c_double, P, P]),
         "pa_step_increment": (i32, [P, P]),
+        "pa_ubp_filter": (i32, [P, i64, i32, f32, f32, P, P]),
+        "pa_ubp": (i32, [G, ctypes.POINTER(ctypes.c_float), P, ctypes.POINTER(pa_grid), P, P]),
+        "pa_splat": (i32, [B, f32, ctypes.POINTER(pa_grid), P, P]),
+        "pa_map": (i32, [P, ctypes.POINTER(pa_grid), P, P, P, P]),
+        "pa_ssim_workspace_size": (sz, [i32, i32]),
+        "pa_ssim": (i32, [P, P, i32, i32, f32, u32, P, P, P, sz, P]),
     }
     for name, (res, args) in sig.items():
         fn = getattr(lib, name)
@@ -126,4 +138,5 @@ def exported_symbols() -> list[str]:
             "pa_forward_workspace_size_ex", "pa_forward", "pa_forward_ex", "pa_forward_plan_info", "pa_adjoint",
             "pa_batched_workspace_size", "pa_forward_batched", "pa_adjoint_batched",
             "pa_loss_workspace_size", "pa_residual_loss", "pa_residual_loss_noalloc", "pa_sumsq", "pa_count_contributions", "pa_adam_step",
-            "pa_adam_step_scheduled", "pa_step_increment"]
+            "pa_adam_step_scheduled", "pa_step_increment", "pa_ubp_filter", "pa_ubp", "pa_splat", "pa_map",
+            "pa_ssim_workspace_size", "pa_ssim"]

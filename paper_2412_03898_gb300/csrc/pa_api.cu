@@ -67,6 +67,13 @@ int check_canon(const pa_canon *c) {
   return PA_OK;
 }
 
+int check_grid(const pa_grid *g) {
+  if (g == nullptr || !(g->h > 0.f) || g->nx < 1 || g->ny < 1 || g->nz < 1) return PA_ERR_INVALID_ARG;
+  if (!std::isfinite(g->origin[0]) || !std::isfinite(g->origin[1]) || !std::isfinite(g->origin[2]))
+    return PA_ERR_INVALID_ARG;
+  return PA_OK;
+}
+
 pa::Acq make_acq(const pa_geom *g) {
   pa::Acq q;
   q.sensors = g->sensors;
@@ -509,6 +516,114 @@ int32_t pa_adam_step_scheduled(float *x, const float *g, float *m, float *v, int
 int32_t pa_step_increment(int32_t *step, void *stream) {
   if (step == nullptr) return PA_ERR_INVALID_ARG;
   return cuda_status(pa::launch_step_increment(step, static_cast<cudaStream_t>(stream)));
+}
+
+
+// ---------------------------------------------------------------------------
+// Imaging.
+
+int32_t pa_ubp_filter(const float *traces, int64_t n_traces, int32_t n_samples, float fs, float t0, float *b,
+                      void *stream) {
+  if (n_traces < 0 || n_samples < 2 || !(fs > 0.f) || !std::isfinite(t0)) return PA_ERR_INVALID_ARG;
+  if (n_traces == 0) return PA_OK;
+  if (traces == nullptr || b == nullptr || traces == b) return PA_ERR_INVALID_ARG;
+  if (!dev_info()) return PA_ERR_CUDA;
+  return cuda_status(pa::launch_ubp_filter(traces, n_traces, n_samples, fs, t0, b, static_cast<cudaStream_t>(stream)));
+}
+
+int32_t pa_ubp(const pa_geom *geom, const float *center, const float *b, const pa_grid *grid, float *vol,
+               void *stream) {
+  int rc = check_geom(geom);
+  if (rc) return rc;
+  if ((rc = check_grid(grid))) return rc;
+  if (center == nullptr || b == nullptr || vol == nullptr) return PA_ERR_INVALID_ARG;
+  if (!dev_info()) return PA_ERR_CUDA;
+  pa::UbpArgs a;
+  a.b = b;
+  a.sensors = geom->sensors;
+  a.S = geom->n_sensors;
+  a.sstride = geom->sensor_stride;
+  a.T = geom->n_samples;
+  a.cx = center[0];
+  a.cy = center[1];
+  a.cz = center[2];
+  a.fs_c = (float)((double)geom->fs / (double)geom->c);
+  a.t0_fs = (float)((double)geom->t0 * (double)geom->fs);
+  a.ox = grid->origin[0];
+  a.oy = grid->origin[1];
+  a.oz = grid->origin[2];
+  a.h = grid->h;
+  a.nx = grid->nx;
+  a.ny = grid->ny;
+  a.nz = grid->nz;
+  a.vol = vol;
+  return cuda_status(pa::launch_ubp(a, static_cast<cudaStream_t>(stream)));
+}
+
+int32_t pa_splat(const pa_balls *balls, float kappa, const pa_grid *grid, float *vol, void *stream) {
+  int rc = check_balls(balls);
+  if (rc) return rc;
+  if ((rc = check_grid(grid))) return rc;
+  if (!(kappa > 0.f) || vol == nullptr) return PA_ERR_INVALID_ARG;
+  if (!dev_info()) return PA_ERR_CUDA;
+  pa::SplatArgs a;
+  a.state = balls->state;
+  a.n = balls->n;
+  a.stride = balls->stride;
+  a.kappa = kappa;
+  a.ox = grid->origin[0];
+  a.oy = grid->origin[1];
+  a.oz = grid->origin[2];
+  a.h = grid->h;
+  a.nx = grid->nx;
+  a.ny = grid->ny;
+  a.nz = grid->nz;
+  a.vol = vol;
+  return cuda_status(pa::launch_splat(a, static_cast<cudaStream_t>(stream)));
+}
+
+int32_t pa_map(const float *vol, const pa_grid *grid, float *xy, float *yz, float *xz, void *stream) {
+  int rc = check_grid(grid);
+  if (rc) return rc;
+  if (vol == nullptr) return PA_ERR_INVALID_ARG;
+  if (!dev_info()) return PA_ERR_CUDA;
+  return cuda_status(pa::launch_map(vol, grid->nx, grid->ny, grid->nz, xy, yz, xz, static_cast<cudaStream_t>(stream)));
+}
+
+size_t pa_ssim_workspace_size(int32_t H, int32_t W) {
+  if (H < 11 || W < 11) return 0;
+  // normalisation (16 B) + min/max partials + FP64 SSIM partials
+  return 16 + sizeof(float4) * (size_t)pa::minmax_partials() + sizeof(double) * (size_t)pa::ssim_blocks(H, W);
+}
+
+int32_t pa_ssim(const float *x, const float *y, int32_t H, int32_t W, float L, uint32_t flags, float *map,
+                double *mean, void *workspace, size_t workspace_bytes, void *stream) {
+  if ((flags & ~PA_SSIM_MINMAX) != 0) return PA_ERR_INVALID_ARG;
+  if (flags & PA_SSIM_MINMAX) L = 1.f;
+  if (H < 11 || W < 11 || !(L > 0.f) || x == nullptr || y == nullptr || mean == nullptr) return PA_ERR_INVALID_ARG;
+  if (workspace == nullptr || workspace_bytes < pa_ssim_workspace_size(H, W) || !aligned(workspace, 16))
+    return PA_ERR_WORKSPACE;
+  if (!dev_info()) return PA_ERR_CUDA;
+  pa::SsimArgs a;
+  a.x = x;
+  a.y = y;
+  a.H = H;
+  a.W = W;
+  a.C1 = (float)((0.01 * (double)L) * (0.01 * (double)L));
+  a.C2 = (float)((0.03 * (double)L) * (0.03 * (double)L));
+  double g[11], gs = 0.0;
+  for (int i = 0; i < 11; ++i) {
+    g[i] = std::exp(-((i - 5) * (i - 5)) / (2.0 * 1.5 * 1.5));
+    gs += g[i];
+  }
+  for (int i = 0; i < 11; ++i) a.g[i] = (float)(g[i] / gs);
+  a.map = map;
+  char *ws = static_cast<char *>(workspace);
+  float4 *norm = reinterpret_cast<float4 *>(ws);
+  float4 *mm = reinterpret_cast<float4 *>(ws + 16);
+  a.partials = reinterpret_cast<double *>(ws + 16 + sizeof(float4) * (size_t)pa::minmax_partials());
+  a.norm = (flags & PA_SSIM_MINMAX) ? norm : nullptr;
+  return cuda_status(pa::launch_ssim(a, mean, mm, static_cast<cudaStream_t>(stream)));
 }
 
 }  // extern "C"

@@ -112,6 +112,47 @@ cudaError_t launch_count(const Acq &q, const float *state, long long n, long lon
                          unsigned long long *out, cudaStream_t st);
 cudaError_t launch_adjoint_static(const AdjArgs &a, int sms, cudaStream_t st);
 cudaError_t launch_adjoint_4d(const AdjArgs &a, int sms, cudaStream_t st);
+// Imaging kernels (pa_image.cu).
+struct UbpArgs {
+  const float *b;        // filtered traces [S][T]
+  const float *sensors;  // [3][sstride]
+  int S, sstride, T;
+  float cx, cy, cz;      // array centre (the sensors' inward normals point at it)
+  float fs_c;            // fs / c: samples per mm
+  float t0_fs;           // t0 * fs
+  float ox, oy, oz, h;   // grid origin and spacing
+  int nx, ny, nz;
+  float *vol;            // [nz][ny][nx]
+};
+
+struct SplatArgs {
+  const float *state;  // [5][stride]
+  long long n, stride;
+  float kappa;
+  float ox, oy, oz, h;
+  int nx, ny, nz;
+  float *vol;
+};
+
+struct SsimArgs {
+  const float *x, *y;  // [H][W]
+  int H, W;
+  float C1, C2;
+  float g[11];         // normalised 1D Gaussian window (sigma 1.5)
+  float *map;          // [(H-10)][(W-10)] or nullptr
+  double *partials;    // one per CTA
+  const float4 *norm;  // (x offset, x scale, y offset, y scale) applied on load, or nullptr
+};
+
+cudaError_t launch_ubp_filter(const float *p, long long n_traces, int T, float fs, float t0, float *b,
+                              cudaStream_t st);
+cudaError_t launch_ubp(const UbpArgs &a, cudaStream_t st);
+cudaError_t launch_splat(const SplatArgs &a, cudaStream_t st);
+cudaError_t launch_map(const float *v, int nx, int ny, int nz, float *xy, float *yz, float *xz, cudaStream_t st);
+int ssim_blocks(int H, int W);
+int minmax_partials();
+cudaError_t launch_ssim(const SsimArgs &a, double *out, float4 *minmax_ws, cudaStream_t st);
+
 cudaError_t launch_deform_backward(const float *canon, const float *omega, const float *theta, const float *sigma,
                                    long long n, long long stride, int nb, const float *t, int F, const float *gstate,
                                    float *g_canon, float *g_omega, float *g_theta, float *g_sigma, bool acc,

@@ -175,3 +175,11 @@ def test_ssim_matches_an_independent_separable_gaussian_filter():
     got, gmap = oracle.ssim(x, y, L, want_map=True)
     np.testing.assert_allclose(gmap, m, rtol=0, atol=1e-12)
     assert got == pytest.approx(m.mean(), abs=1e-12)
+
+
+def test_ssim_minmax_is_invariant_to_affine_intensity_changes():
+    rng = np.random.default_rng(8)
+    x = rng.random((30, 30))
+    y = np.clip(x + 0.1 * rng.standard_normal(x.shape), 0, 1)
+    base = oracle.ssim(oracle.minmax01(x), oracle.minmax01(y), 1.0)
+    assert oracle.ssim(5.0 * x - 2.0, 0.01 * y + 7.0, minmax=True) == pytest.approx(base, abs=1e-12)
