@@ -89,6 +89,8 @@ def parse():
     ap.add_argument("--steps-batched", type=int, default=2)
     ap.add_argument("--no-autotune", action="store_true")
     ap.add_argument("--no-imaging", action="store_true", help="skip the UBP / splat / MAP / SSIM leg")
+    ap.add_argument("--ir-quality-iters", type=int, default=160,
+                    help="IR iterations of the 4D reconstruction-quality leg (0 = skip)")
     a = ap.parse_args()
     a.warmup = max(a.warmup, 3)
     return a
@@ -358,6 +360,9 @@ def run_ours(args):
     imaging = None
     if not args.no_imaging:
         imaging = bench_imaging(args, pa, pa_inputs, dev, flush)
+    ir_quality = None
+    if args.ir_quality_iters > 0 and not args.no_4d:
+        ir_quality = bench_ir_quality(args, pa, pa_inputs, dev)
     clocks = sampler.stop()
 
     fwd_avg = statistics.mean(t_fwd)
@@ -395,6 +400,8 @@ def run_ours(args):
         line["batched"] = batched
     if imaging is not None:
         line["imaging"] = imaging
+    if ir_quality is not None:
+        line["ir_quality"] = ir_quality
     if rank == 0 and world == 1 and not args.no_cpu:
         line["cpu_baseline"] = cpu_baseline(sc)
     if rank == 0:
@@ -504,6 +511,71 @@ def bench_imaging(args, pa, pa_inputs, dev, flush):
     out["ubp_vs_gt_map_ssim"] = {k: float(pa.ssim(u, g, minmax=True)) for k, u, g in zip(("xy", "yz", "xz"), mu, mg)}
     pa.device_error()
     return out
+
+
+def bench_ir_quality(args, pa, pa_inputs, dev):
+    """Reconstruction quality of the 4D IR loop (Sec. 2.2 stage 2, Sec. 3.2
+    hyper-parameters) on 4d-100k-20f: the canonical cloud starts at the
+    ground-truth frame 0 with zero deformation, the measurements are the
+    forward projections of the 20 ground-truth frames (radial pulsation and
+    drift), and the whole iteration replays from one CUDA graph.  Reports the
+    loss, the RMS position error against the ground-truth motion, and the SSIM
+    of XY / YZ / XZ MAPs of the splatted model against the splatted ground
+    truth at the first, middle and last frames, next to UBP from the same
+    576-sensor measurements (the paper's Tab. 1 columns, on synthetic data)."""
+    import torch
+    from paper_2412_03898_gb300.ir import GGBallIR, init_deformation
+    sc = pa_inputs.config_scene(3)
+    n, F = sc.n_balls, sc.n_frames
+    to_dev = lambda a: pa.pad_last(torch.from_numpy(np.ascontiguousarray(a, dtype=np.float32)).to(dev))
+    geom = pa.Geometry(torch.from_numpy(sc.sensors).to(dev), sc.c, sc.fs, sc.t0, sc.n_samples, sc.kappa)
+    gt = to_dev(sc.frames).contiguous()
+    meas = pa.forward(geom, gt, n)
+    t = torch.from_numpy(pa_inputs.frame_times(F)).to(dev)
+    canon = to_dev(sc.frames[0]).contiguous()
+    deform = init_deformation(65, canon.shape[-1], dev)
+    ir = GGBallIR(geom, canon, deform, t, meas, n)
+    grid = pa.Grid.cube(15.0, 192)
+    frames = [0, F // 2, F - 1]
+    vol = torch.empty(grid.shape, dtype=torch.float32, device=dev)
+    ref = torch.empty_like(vol)
+    bfilt = torch.empty(geom.n_sensors, geom.n_samples, dtype=torch.float32, device=dev)
+
+    def gt_maps(f):
+        pa.splat(gt[f], grid, sc.kappa, n, out=ref)
+        return pa.maps(ref, grid)
+
+    gt_m = {f: [m.clone() for m in gt_maps(f)] for f in frames}
+
+    def model_quality():
+        state = pa.deform_balls(ir.canon, ir.deform[0], ir.deform[1], ir.deform[2], t, n)
+        err = (state[:, :3, :n] - gt[:, :3, :n]).pow(2).sum(1).mean().sqrt().item()
+        ss = {}
+        for f in frames:
+            pa.splat(state[f], grid, sc.kappa, n, out=vol)
+            ss[f] = [float(pa.ssim(u, g, minmax=True)) for u, g in zip(pa.maps(vol, grid), gt_m[f])]
+        return err, ss
+
+    pos0, ss0 = model_quality()
+    loss0 = float(ir.step().sum())
+    ir.capture()
+    for _ in range(args.ir_quality_iters - 2):
+        ir.step_graph()
+    loss1 = float(ir.loss.sum())
+    pos1, ss1 = model_quality()
+    ubp = {}
+    for f in frames:
+        pa.ubp_filter(meas[f], sc.fs, sc.t0, out=bfilt)
+        pa.ubp(geom, bfilt, grid, out=vol)
+        ubp[f] = [float(pa.ssim(u, g, minmax=True)) for u, g in zip(pa.maps(vol, grid), gt_m[f])]
+    pa.device_error()
+    views = ("xy", "yz", "xz")
+    fmt = lambda d: {f"frame{f + 1}": dict(zip(views, v)) for f, v in d.items()}
+    return {"workload": f"{sc.name}: {n} balls, {F} frames, Nb = 65, {geom.n_sensors} sensors; MAPs on "
+                        f"{grid.shape[0]}^3 x {grid.h:.3f} mm",
+            "iterations": args.ir_quality_iters, "loss_first": loss0, "loss_last": loss1,
+            "position_rmse_mm_first": pos0, "position_rmse_mm_last": pos1,
+            "map_ssim_4d_before": fmt(ss0), "map_ssim_4d_after": fmt(ss1), "map_ssim_ubp": fmt(ubp)}
 
 
 def bench_batched(args, pa, pa_inputs, dev, flush):

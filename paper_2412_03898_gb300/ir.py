@@ -30,11 +30,16 @@ import torch
 from . import (Geometry, adam_step_scheduled, adjoint, deform_backward, deform_balls, forward, residual_loss,
                step_increment)
 
-# Sec. 3.2: initial learning rates and step decay.
-LR_COORD = 5e-7
+# Sec. 3.2: initial learning rates and step decay.  The paper states the
+# rates without units.  Lengths here are in mm, and the coordinate and size
+# rates are read as SI metres (5e-7 m = 5e-4 mm per Adam step): taken as mm
+# they could move a ball by under 1e-4 mm over the whole decay schedule.  The
+# pressure and the dimensionless deformation coefficients keep their numbers.
+LR_COORD = 5e-7    # m
 LR_PRESSURE = 5e-4
-LR_STD = 5e-7
+LR_STD = 5e-7      # m
 LR_DEFORM = 5e-6
+MM_PER_M = 1e3
 STEP_SIZE = 160
 DROP_RATE = 0.1
 
@@ -47,7 +52,7 @@ class GGBallIR:
     omega, theta, sigma; t_frames: [F]; meas: [F, S, T]."""
 
     def __init__(self, geom: Geometry, canon: torch.Tensor, deform: torch.Tensor, t_frames: torch.Tensor,
-                 meas: torch.Tensor, n: Optional[int] = None, fused: bool = False):
+                 meas: torch.Tensor, n: Optional[int] = None, fused: bool = False, lr_scale: float = 1.0):
         self.geom = geom
         self.canon = canon
         self.deform = deform
@@ -66,6 +71,7 @@ class GGBallIR:
         self.resid = torch.empty_like(self.traces)
         self.loss = torch.empty(self.F, dtype=torch.float64, device=dev)
         self.fused = fused
+        self.lr_scale = float(lr_scale)
         self.g_state = None if fused else torch.empty(self.F, 5, stride, dtype=torch.float32, device=dev)
         self.step_count = 0
         self.step_dev = torch.zeros(1, dtype=torch.int32, device=dev)
@@ -107,11 +113,11 @@ class GGBallIR:
         self.step_count += 1
         assert LR_COORD == LR_STD  # x, y, z and a rows share one launch
         for lr0, x, g, m, v in (
-                (LR_COORD, self.canon[:4], self.g_canon[:4], self.m_canon[:4], self.v_canon[:4]),
+                (LR_COORD * MM_PER_M, self.canon[:4], self.g_canon[:4], self.m_canon[:4], self.v_canon[:4]),
                 (LR_PRESSURE, self.canon[4], self.g_canon[4], self.m_canon[4], self.v_canon[4]),
                 (LR_DEFORM, self.deform, self.g_deform, self.m_deform, self.v_deform)):
-            adam_step_scheduled(x.reshape(-1), g.reshape(-1), m.reshape(-1), v.reshape(-1), lr0, self.step_dev,
-                                STEP_SIZE, DROP_RATE)
+            adam_step_scheduled(x.reshape(-1), g.reshape(-1), m.reshape(-1), v.reshape(-1), lr0 * self.lr_scale,
+                                self.step_dev, STEP_SIZE, DROP_RATE)
 
     def _ensure_workspace(self):
         from . import forward_workspace_size
