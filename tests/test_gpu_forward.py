@@ -26,7 +26,8 @@ def _oracle_traces(sc, state=None):
     return y, n
 
 
-@pytest.mark.parametrize("tiles", [None, (8, 256, 128, 3, 4), (5, 1024, 64, 1, 1), (16, 128, 512, 2, 8), (1, 1028, 4, 7, 2)])
+@pytest.mark.parametrize("tiles", [None, (8, 256, 128, 3, 4), (5, 1024, 64, 1, 1), (16, 128, 512, 2, 8), (1, 1028, 4, 7, 2),
+                                   (12, 1536, 384, 0, 16)])
 def test_forward_parity_tiles(pa, tiles):
     sc = pa_inputs.small_scene(seed=1, n_balls=1003, n_sensors=37, n_samples=1028)
     geom = geometry(sc)
@@ -37,6 +38,18 @@ def test_forward_parity_tiles(pa, tiles):
     got = y.cpu().numpy()
     assert rel_l2(got, y_o) <= TRACE_TOL
     assert max_rel_elem(got, y_o) <= 2e-5
+
+
+@pytest.mark.parametrize("group", [8, 1])
+def test_forward_long_windows(pa, group):
+    # kappa = 8 and 0.5-0.9 mm balls: windows of 210-380 samples, many
+    # 32-sample steps per group
+    sc = pa_inputs.small_scene(seed=9, n_balls=301, n_sensors=13, n_samples=1536, a_range=(0.5, 0.9), kappa=8.0)
+    geom = geometry(sc)
+    y = pa.forward(geom, dev_pad(sc.balls)[None], sc.n_balls, tiles=(8, 1536, 128, 0, group))
+    pa.device_error()
+    y_o, _ = _oracle_traces(sc)
+    assert rel_l2(y.cpu().numpy(), y_o) <= TRACE_TOL
 
 
 def test_forward_multiframe_and_accumulate(pa):
