@@ -7,14 +7,14 @@
 //  - One warp owns one ball (static mode: one (frame, ball) item) and loops
 //    over all sensors.  The 32 lanes compute the window, phase and gradient
 //    factors of 32 (ball, sensor) pairs in parallel and publish them,
-//    compacted, in shared memory; the warp then walks eight pairs at a time,
-//    one per 4-lane sub-warp, each lane on four consecutive samples per step
-//    (a float4 residual load from L2, packed FP32x2 arithmetic, next step's
-//    load in flight), accumulating per lane
+//    compacted, in shared memory; the warp then walks sixteen pairs at a
+//    time, one per 2-lane sub-warp, each lane on four consecutive samples
+//    per step (a float4 residual load from L2, packed FP32x2 arithmetic,
+//    next step's load in flight), accumulating per lane
 //        S1 = sum g E u,  S3 = sum g E u^3,  SR = sum g E (1 - tau^2/a^2)
-//    which a 4-lane shuffle reduction turns into the pair's sums; the
-//    sub-warp's first lane folds them with the pair's factors into its
-//    gradient accumulators.
+//    which one shuffle between the sub-warp's two lanes turns into the
+//    pair's sums; the sub-warp's first lane folds them with the pair's
+//    factors into its gradient accumulators.
 //  - A warp-shuffle reduction over lanes (i.e. over sensors and samples) at
 //    the end of the ball gives dL/d(x, y, z, a, p); one lane writes it.
 //  - 4D mode recomputes the deformed state of the ball per frame in registers
@@ -76,15 +76,17 @@ __device__ __forceinline__ void ball_frame_grad(const Acq &q, const float *gfram
         rec[3 * pos + 2] = r2;
       }
       __syncwarp();
-      // Eight pairs at a time, one per 4-lane sub-warp: each sub-warp walks
+      // Sixteen pairs at a time, one per 2-lane sub-warp: each sub-warp walks
       // its pair's whole window, each lane four consecutive samples per step
       // (one float4 residual load, two packed FP32x2 halves), the next step's
-      // load issued before the current step's arithmetic.  Samples of the
-      // aligned float4s outside the window get weight 0 from the window mask
-      // (u^2 <= (kappa K_S)^2, the forward's own test).
-      const int sub = lane >> 2, sl = lane & 3;
+      // load issued before the current step's arithmetic.  All pairs belong
+      // to one ball, so their windows have nearly the same length and the
+      // sub-warps finish together.  Samples of the aligned float4s outside
+      // the window get weight 0 from the window mask (u^2 <= (kappa K_S)^2,
+      // the forward's own test).
+      const int sub = lane >> 1, sl = lane & 1;
       const float2 negk = make_float2(-K_2LN2, -K_2LN2), one = make_float2(1.f, 1.f);
-      for (int g0 = 0; g0 < nv; g0 += 8) {
+      for (int g0 = 0; g0 < nv; g0 += 16) {
         const int i = g0 + sub;
         const bool act = i < nv;
         const int ii = act ? i : 0;
@@ -95,7 +97,7 @@ __device__ __forceinline__ void ball_frame_grad(const Acq &q, const float *gfram
         // a float4 starting at k <= khi <= T - 1 ends at k + 3 <= T - 1
         const int ka = klo & ~3;
         const float4 *row = reinterpret_cast<const float4 *>(gframe + (long long)__float_as_int(a2.w) * T);
-        const int nit = act ? ((khi - ka) >> 4) + 1 : 0;
+        const int nit = act ? ((khi - ka) >> 3) + 1 : 0;
         const int nmax = __reduce_max_sync(FULL, nit);
         int kk = ka + 4 * sl;
         const float du = a0.y;
@@ -104,7 +106,7 @@ __device__ __forceinline__ void ball_frame_grad(const Acq &q, const float *gfram
         ua.y = ua.x - du;
         ub.x = fmaf(-2.f, du, ua.x);
         ub.y = fmaf(-3.f, du, ua.x);
-        const float2 nd2 = make_float2(-16.f * du, -16.f * du);
+        const float2 nd2 = make_float2(-8.f * du, -8.f * du);
         float2 S1 = make_float2(0.f, 0.f), S3 = S1, SR = S1;
         auto half = [&](const float2 u2, const float2 g2) {
           const float2 sq = __fmul2_rn(u2, u2);                                      // u^2
@@ -118,8 +120,8 @@ __device__ __forceinline__ void ball_frame_grad(const Acq &q, const float *gfram
         };
         const float4 zero4 = make_float4(0.f, 0.f, 0.f, 0.f);
         float4 gcur = kk <= khi ? __ldg(row + (kk >> 2)) : zero4;
-        for (int it = 0; it < nmax; ++it, kk += 16) {
-          const float4 gnext = kk + 16 <= khi ? __ldg(row + ((kk + 16) >> 2)) : zero4;
+        for (int it = 0; it < nmax; ++it, kk += 8) {
+          const float4 gnext = kk + 8 <= khi ? __ldg(row + ((kk + 8) >> 2)) : zero4;
           half(ua, make_float2(gcur.x, gcur.y));
           half(ub, make_float2(gcur.z, gcur.w));
           ua = __fadd2_rn(ua, nd2);
@@ -128,11 +130,9 @@ __device__ __forceinline__ void ball_frame_grad(const Acq &q, const float *gfram
         }
         float s1 = S1.x + S1.y, s3 = S3.x + S3.y, sr = SR.x + SR.y;
 #pragma unroll
-        for (int o = 2; o > 0; o >>= 1) {
-          s1 += __shfl_xor_sync(FULL, s1, o);
-          s3 += __shfl_xor_sync(FULL, s3, o);
-          sr += __shfl_xor_sync(FULL, sr, o);
-        }
+        s1 += __shfl_xor_sync(FULL, s1, 1);
+        s3 += __shfl_xor_sync(FULL, s3, 1);
+        sr += __shfl_xor_sync(FULL, sr, 1);
         if (sl == 0 && act) {
           const float4 a1 = rec[3 * ii + 1];
           gp = fmaf(s1, a0.z, gp);
