@@ -48,11 +48,25 @@ __global__ void __launch_bounds__(256) k_ubp_filter(const float *__restrict__ p,
 }
 
 // ---------------------------------------------------------------------------
-// UBP back-projection.  One thread per voxel, CTA = an 8 x 8 x 4 brick (x
-// fastest), so the 32 voxels of a warp are close together and read each
-// sensor's filtered trace from one or two L1 lines.  Sensor positions and unit
-// inward normals are staged in shared memory, kUbpChunk sensors at a time.
+// UBP back-projection.  CTA = an 8 x 8 x 8 brick (x fastest), 256 threads;
+// thread (tx, ty, tz) owns voxels (tx, ty, tz) and (tx, ty, tz + 4), which
+// share the sensor loads, dx, dy and the in-plane partial sums, the rest of
+// the arithmetic running on both as packed FP32x2.  The 32 voxels of a warp
+// are close together, so each sensor's filtered trace is read from one or two
+// L1 lines.  Sensor positions and unit inward normals are staged in shared
+// memory, kUbpChunk sensors at a time.
 constexpr int kUbpChunk = 1024;
+
+__device__ __forceinline__ float ubp_interp(const float *brow, float f, float hi_f) {
+  const float fl = floorf(f);
+  float val = 0.f;
+  if (fl >= 0.f && fl <= hi_f) {  // false for NaN
+    const int i = (int)fl;
+    const float v0 = __ldg(brow + i), v1 = __ldg(brow + i + 1);
+    val = fmaf(f - fl, v1 - v0, v0);
+  }
+  return val;
+}
 
 __global__ void __launch_bounds__(256) k_ubp(const UbpArgs A) {
   __shared__ float4 s_pos[kUbpChunk];
@@ -60,11 +74,13 @@ __global__ void __launch_bounds__(256) k_ubp(const UbpArgs A) {
   const int tid = threadIdx.x;
   const int ix = blockIdx.x * 8 + (tid & 7);
   const int iy = blockIdx.y * 8 + ((tid >> 3) & 7);
-  const int iz = blockIdx.z * 4 + (tid >> 6);
-  const bool ok = ix < A.nx && iy < A.ny && iz < A.nz;
-  const float rx = fmaf((float)ix, A.h, A.ox), ry = fmaf((float)iy, A.h, A.oy), rz = fmaf((float)iz, A.h, A.oz);
+  const int iz = blockIdx.z * 8 + (tid >> 6);  // and iz + 4
+  const bool okxy = ix < A.nx && iy < A.ny;
+  const float rx = fmaf((float)ix, A.h, A.ox), ry = fmaf((float)iy, A.h, A.oy);
+  const float2 rz = make_float2(fmaf((float)iz, A.h, A.oz), fmaf((float)(iz + 4), A.h, A.oz));
   const float hi_f = (float)(A.T - 2);
-  float num = 0.f, den = 0.f;
+  const float2 fsc2 = make_float2(A.fs_c, A.fs_c), mt2 = make_float2(-A.t0_fs, -A.t0_fs);
+  float2 num = make_float2(0.f, 0.f), den = num;
   for (int s0 = 0; s0 < A.S; s0 += kUbpChunk) {
     const int cnt = min(kUbpChunk, A.S - s0);
     __syncthreads();  // the previous chunk is consumed
@@ -77,32 +93,32 @@ __global__ void __launch_bounds__(256) k_ubp(const UbpArgs A) {
       s_nrm[j] = make_float4(nx * inv, ny * inv, nz * inv, 0.f);
     }
     __syncthreads();
-    if (ok) {
+    if (okxy) {
       const float *brow = A.b + (long long)s0 * A.T;
       for (int j = 0; j < cnt; ++j, brow += A.T) {
         const float4 sp = s_pos[j], sn = s_nrm[j];
-        const float dx = rx - sp.x, dy = ry - sp.y, dz = rz - sp.z;
-        const float d2 = fmaf(dx, dx, fmaf(dy, dy, dz * dz));
-        const float dot = fmaf(sn.x, dx, fmaf(sn.y, dy, sn.z * dz));
-        if (dot > 0.f) {
-          const float ir = rsqrtf(d2);
-          const float d = d2 * ir;
-          const float w = dot * ir * ir * ir;  // cos(theta) / d^2
-          const float f = fmaf(d, A.fs_c, -A.t0_fs);
-          const float fl = floorf(f);
-          float val = 0.f;
-          if (fl >= 0.f && fl <= hi_f) {
-            const int i = (int)fl;
-            const float v0 = __ldg(brow + i), v1 = __ldg(brow + i + 1);
-            val = fmaf(f - fl, v1 - v0, v0);
-          }
-          num = fmaf(w, val, num);
-          den += w;
-        }
+        const float dx = rx - sp.x, dy = ry - sp.y;
+        const float dxy = fmaf(dx, dx, dy * dy);
+        const float nxy = fmaf(sn.x, dx, sn.y * dy);
+        const float2 dz = __fadd2_rn(rz, make_float2(-sp.z, -sp.z));
+        const float2 d2 = __ffma2_rn(dz, dz, make_float2(dxy, dxy));
+        const float2 dot = __ffma2_rn(make_float2(sn.z, sn.z), dz, make_float2(nxy, nxy));
+        const float2 ir = make_float2(rsqrtf(d2.x), rsqrtf(d2.y));
+        const float2 d = __fmul2_rn(d2, ir);
+        float2 w = __fmul2_rn(__fmul2_rn(dot, ir), __fmul2_rn(ir, ir));  // cos(theta) / d^2
+        w.x = dot.x > 0.f ? w.x : 0.f;  // sensors facing away are left out
+        w.y = dot.y > 0.f ? w.y : 0.f;
+        const float2 f = __ffma2_rn(d, fsc2, mt2);
+        const float2 val = make_float2(ubp_interp(brow, f.x, hi_f), ubp_interp(brow, f.y, hi_f));
+        num = __ffma2_rn(w, val, num);
+        den = __fadd2_rn(den, w);
       }
     }
   }
-  if (ok) A.vol[((long long)iz * A.ny + iy) * A.nx + ix] = den > 0.f ? num / den : 0.f;
+  if (okxy) {
+    if (iz < A.nz) A.vol[((long long)iz * A.ny + iy) * A.nx + ix] = den.x > 0.f ? num.x / den.x : 0.f;
+    if (iz + 4 < A.nz) A.vol[((long long)(iz + 4) * A.ny + iy) * A.nx + ix] = den.y > 0.f ? num.y / den.y : 0.f;
+  }
 }
 
 // ---------------------------------------------------------------------------
@@ -381,7 +397,7 @@ cudaError_t launch_ubp_filter(const float *p, long long n_traces, int T, float f
 
 cudaError_t launch_ubp(const UbpArgs &a, cudaStream_t st) {
   if ((long long)a.nx * a.ny * a.nz == 0) return cudaSuccess;
-  dim3 grid((a.nx + 7) / 8, (a.ny + 7) / 8, (a.nz + 3) / 4);
+  dim3 grid((a.nx + 7) / 8, (a.ny + 7) / 8, (a.nz + 7) / 8);
   k_ubp<<<grid, 256, 0, st>>>(a);
   return cudaGetLastError();
 }
