@@ -198,21 +198,31 @@ __global__ void __launch_bounds__(32 * kAdjWarps) k_adjoint_static(const AdjArgs
   if (dom) set_error(A.err, PA_ERR_DOMAIN);
 }
 
-// 4D mode: item = ball; frames looped inside.
-__global__ void __launch_bounds__(32 * kAdjWarps) k_adjoint_4d(const AdjArgs A) {
+// 4D mode: item = ball; frames looped inside, in chunks of kAdj4dFrames.
+// Pass 1 (per frame): H of Eq. 2 for the 5 channels (lanes over basis
+// functions), the deformed state of Eq. 1, the state gradient of the ball at
+// that frame, and its share of the canonical gradient; the scaled frame
+// gradients g_c(f) q0_c go to a per-warp buffer.  Pass 2: lanes over the
+// (channel, basis) slots sum the chain rule over the buffered frames and write
+// each (omega, theta, sigma) gradient once per chunk.  The deformation
+// parameters are read through L1/L2 rather than held in shared memory, which
+// keeps the block at ~30 KB of shared memory and 4 blocks per SM.
+constexpr int kAdj4dFrames = 32;
+
+__global__ void __launch_bounds__(32 * kAdjWarps, 4) k_adjoint_4d(const AdjArgs A) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   const int nb = A.nb;
   const int per = 5 * nb;
   float4 *recs = reinterpret_cast<float4 *>(smem_raw);
   float *ssens = reinterpret_cast<float *>(recs + kAdjWarps * 96);
-  float *wbase = ssens + 3 * A.q.S;  // per warp: om, th, isg, gom, gth, gsg  (6 * per floats)
+  float *gbase = ssens + 3 * A.q.S;  // per warp: [kAdj4dFrames][5] scaled frame gradients
   load_sensors(A, ssens);
   __syncthreads();
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   float4 *rec = recs + warp * 96;
-  float *om = wbase + (size_t)warp * 6 * per;
-  float *th = om + per, *isg = th + per, *gom = isg + per, *gth = gom + per, *gsg = gth + per;
+  float *gq = gbase + warp * (kAdj4dFrames * 5);
   const float L2E_HALF = 0.72134752044448170368f;  // log2(e)/2
+  const bool acc = (A.flags & PA_ACCUMULATE) != 0;
   bool dom = false;
   for (long long b = (long long)blockIdx.x * kAdjWarps + warp; b < A.n_items;
        b += (long long)gridDim.x * kAdjWarps) {
@@ -220,57 +230,73 @@ __global__ void __launch_bounds__(32 * kAdjWarps) k_adjoint_4d(const AdjArgs A) 
     float q0[5];
 #pragma unroll
     for (int c = 0; c < 5; ++c) q0[c] = __shfl_sync(FULL, mine, c);
-    for (int i = lane; i < per; i += 32) {
-      const long long gi = (long long)i * A.stride + b;  // [ch][n] rows are contiguous in i
-      om[i] = A.omega[gi];
-      th[i] = A.theta[gi];
-      const float sg = A.sigma[gi];
-      if (!(sg > 0.f)) dom = true;
-      isg[i] = sg > 0.f ? 1.f / sg : 0.f;
-      gom[i] = 0.f;
-      gth[i] = 0.f;
-      gsg[i] = 0.f;
-    }
-    __syncwarp();
     float gcan[5] = {0.f, 0.f, 0.f, 0.f, 0.f};
-    for (int f = 0; f < A.F; ++f) {
-      const float t = __ldg(A.t_frames + f);
-      float H[5];
+    for (int f0 = 0; f0 < A.F; f0 += kAdj4dFrames) {
+      const int fc = min(kAdj4dFrames, A.F - f0);
+      // pass 1
+      for (int j = 0; j < fc; ++j) {
+        const int f = f0 + j;
+        const float t = __ldg(A.t_frames + f);
+        float H[5];
 #pragma unroll
-      for (int c = 0; c < 5; ++c) {
-        float h = 0.f;
-        for (int n = lane; n < nb; n += 32) {
-          const int i = c * nb + n;
-          const float d = (t - th[i]) * isg[i];
-          h = fmaf(om[i], ex2(-d * d * L2E_HALF), h);
+        for (int c = 0; c < 5; ++c) {
+          float h = 0.f;
+          for (int n = lane; n < nb; n += 32) {
+            const long long gi = (long long)(c * nb + n) * A.stride + b;
+            const float sg = __ldg(A.sigma + gi);
+            if (sg > 0.f) {
+              const float d = (t - __ldg(A.theta + gi)) / sg;
+              h = fmaf(__ldg(A.omega + gi), ex2(-d * d * L2E_HALF), h);
+            } else {
+              dom = true;  // term skipped, as in pa_deform_balls
+            }
+          }
+          H[c] = warp_sum(h);
         }
-        H[c] = warp_sum(h);
-      }
-      float g[5];
-      ball_frame_grad(A.q, A.g + (long long)f * A.q.S * A.q.T, ssens, A.q.S, rec, lane, q0[0] * (1.f + H[0]),
-                      q0[1] * (1.f + H[1]), q0[2] * (1.f + H[2]), q0[3] * (1.f + H[3]), q0[4] * (1.f + H[4]), g,
-                      dom);
-      const float sc = A.frame_scale ? __ldg(A.frame_scale + f) : 1.f;
+        float g[5];
+        ball_frame_grad(A.q, A.g + (long long)f * A.q.S * A.q.T, ssens, A.q.S, rec, lane, q0[0] * (1.f + H[0]),
+                        q0[1] * (1.f + H[1]), q0[2] * (1.f + H[2]), q0[3] * (1.f + H[3]), q0[4] * (1.f + H[4]), g,
+                        dom);
+        const float sc = A.frame_scale ? __ldg(A.frame_scale + f) : 1.f;
 #pragma unroll
-      for (int c = 0; c < 5; ++c) {
-        const float gc = g[c] * sc;
-        gcan[c] = fmaf(gc, 1.f + H[c], gcan[c]);
-        const float gq = gc * q0[c];
-        for (int n = lane; n < nb; n += 32) {
-          const int i = c * nb + n;
-          const float is = isg[i];
-          const float d = (t - th[i]) * is;          // (t - theta)/sigma
-          const float bn = ex2(-d * d * L2E_HALF);   // basis value
-          const float w = gq * bn;
-          gom[i] += w;
-          const float wo = w * om[i];
-          gth[i] = fmaf(wo, d * is, gth[i]);         // (t - theta)/sigma^2
-          gsg[i] = fmaf(wo, d * d * is, gsg[i]);     // (t - theta)^2/sigma^3
+        for (int c = 0; c < 5; ++c) {
+          const float gc = g[c] * sc;
+          gcan[c] = fmaf(gc, 1.f + H[c], gcan[c]);
+          if (lane == c) gq[j * 5 + c] = gc * q0[c];
         }
       }
+      __syncwarp();
+      // pass 2: with d = (t_f - theta)/sigma, b = exp(-d^2/2) and w = g q0 b:
+      // dL/domega += sum w, dL/dtheta += omega/sigma sum w d,
+      // dL/dsigma += omega/sigma sum w d^2
+      for (int i = lane; i < per; i += 32) {
+        const int c = i / nb;
+        const long long gi = (long long)i * A.stride + b;  // [ch][n] rows are contiguous in i
+        const float om = __ldg(A.omega + gi), th = __ldg(A.theta + gi), sg = __ldg(A.sigma + gi);
+        float s0 = 0.f, s1 = 0.f, s2 = 0.f, is = 0.f;
+        if (sg > 0.f) {
+          is = 1.f / sg;
+          for (int j = 0; j < fc; ++j) {
+            const float d = (__ldg(A.t_frames + f0 + j) - th) * is;
+            const float w = gq[j * 5 + c] * ex2(-d * d * L2E_HALF);
+            s0 += w;
+            s1 = fmaf(w, d, s1);
+            s2 = fmaf(w * d, d, s2);
+          }
+        }
+        const float oi = om * is;
+        float vo = s0, vt = oi * s1, vs = oi * s2;
+        if (f0 > 0 || acc) {
+          vo += A.g_omega[gi];
+          vt += A.g_theta[gi];
+          vs += A.g_sigma[gi];
+        }
+        A.g_omega[gi] = vo;
+        A.g_theta[gi] = vt;
+        A.g_sigma[gi] = vs;
+      }
+      __syncwarp();
     }
-    __syncwarp();
-    const bool acc = (A.flags & PA_ACCUMULATE) != 0;
     if (lane < 5) {
       float gv = gcan[0];
 #pragma unroll
@@ -279,13 +305,6 @@ __global__ void __launch_bounds__(32 * kAdjWarps) k_adjoint_4d(const AdjArgs A) 
       float *dst = A.g_state + lane * A.stride + b;
       *dst = acc ? *dst + gv : gv;
     }
-    for (int i = lane; i < per; i += 32) {
-      const long long gi = (long long)i * A.stride + b;
-      A.g_omega[gi] = acc ? A.g_omega[gi] + gom[i] : gom[i];
-      A.g_theta[gi] = acc ? A.g_theta[gi] + gth[i] : gth[i];
-      A.g_sigma[gi] = acc ? A.g_sigma[gi] + gsg[i] : gsg[i];
-    }
-    __syncwarp();
   }
   if (dom) set_error(A.err, PA_ERR_DOMAIN);
 }
@@ -335,7 +354,8 @@ __global__ void __launch_bounds__(32 * kAdjWarps) k_adjoint_batched(const BatchA
 
 size_t adj_static_smem(int S) { return sizeof(float4) * kAdjWarps * 96 + sizeof(float) * 3 * (size_t)S; }
 size_t adj_4d_smem(int S, int nb) {
-  return adj_static_smem(S) + sizeof(float) * (size_t)kAdjWarps * 6 * 5 * nb;
+  (void)nb;
+  return adj_static_smem(S) + sizeof(float) * (size_t)kAdjWarps * kAdj4dFrames * 5;
 }
 
 template <typename K>
