@@ -140,3 +140,30 @@ def test_imaging_rejects_bad_arguments(pa):
         pa.ssim(torch.zeros(10, 10, device="cuda"), torch.zeros(10, 10, device="cuda"))
     with pytest.raises(pa.PAError):
         pa.splat(torch.zeros(5, 4, device="cuda"), g, kappa=0.0)
+
+
+def test_imaging_edge_cases(pa):
+    # empty ball cloud -> zero volume (the output is overwritten)
+    grid = pa.Grid((0.0, 0.0, 0.0), 0.5, (3, 5, 7))
+    vol = torch.full(grid.shape, 9.0, device="cuda")
+    pa.splat(torch.zeros(5, 4, device="cuda"), grid, 5.0, 0, out=vol)
+    assert not torch.any(vol)
+    # one sensor; a grid whose samples all fall past the last one -> zeros
+    sens = np.array([[0.0], [0.0], [-20.0]], dtype=np.float32)
+    b = np.random.default_rng(69).standard_normal((1, 64)).astype(np.float32)
+    geom = pa.Geometry(torch.from_numpy(sens).cuda(), 1.5, 40.0, 0.0, 64, 5.0)
+    near = pa.Grid((0.0, 0.0, -19.5), 0.1, (2, 2, 2))   # d ~ 0.5 mm -> samples ~13
+    far = pa.Grid((0.0, 0.0, 10.0), 0.1, (2, 2, 2))     # d ~ 30 mm -> samples ~800 > 63
+    bt = torch.from_numpy(b).cuda()
+    got = pa.ubp(geom, bt, near).cpu().numpy()
+    want = oracle.ubp(b, sens, np.zeros(3), 1.5, 40.0, 0.0, np.array(near.origin), near.h, near.shape)
+    assert rel_l2(got, want) <= UBP_TOL
+    assert not torch.any(pa.ubp(geom, bt, far))
+    # 1 x 1 x 1 MAPs and an SSIM with a single window position
+    one = torch.tensor([[[2.5]]], device="cuda")
+    for m in pa.maps(one, pa.Grid((0, 0, 0), 1.0, (1, 1, 1))):
+        assert float(m) == 2.5
+    rng = np.random.default_rng(70)
+    x, y = rng.random((11, 11)).astype(np.float32), rng.random((11, 11)).astype(np.float32)
+    got = float(pa.ssim(torch.from_numpy(x).cuda(), torch.from_numpy(y).cuda()))
+    assert abs(got - oracle.ssim(x, y)) <= 1e-5
