@@ -18,7 +18,8 @@ def pytest_configure(config):
 
 def pytest_collection_modifyitems(config, items):
     # GPU tests are skipped (not failed) when no GPU is visible, so that the
-    # CPU suite can run everywhere; on a GPU machine they run and must pass.
+    # CPU suite can run everywhere; with a CUDA device visible they run and
+    # must pass.
     try:
         import torch
         has_gpu = torch.cuda.is_available()
