@@ -89,6 +89,8 @@ def parse():
     ap.add_argument("--steps-batched", type=int, default=2)
     ap.add_argument("--no-autotune", action="store_true")
     ap.add_argument("--no-imaging", action="store_true", help="skip the UBP / splat / MAP / SSIM leg")
+    ap.add_argument("--large4d", action="store_true",
+                    help="add the 1M-ball, 50-frame IR iteration (4d-1m-50f; ~20 GB of device memory)")
     ap.add_argument("--ir-quality-iters", type=int, default=160,
                     help="IR iterations of the 4D reconstruction-quality leg (0 = skip)")
     a = ap.parse_args()
@@ -211,6 +213,25 @@ def cpu_baseline(sc, n_sensors_sample=None, seed=0):
             "sample": f"{sc.name}: all {sc.n_balls} balls x {len(pick)} of {sc.n_sensors} sensors x "
                       f"{sc.n_samples} samples, forward + adjoint in FP64 ({n} contributions, "
                       f"{tf + ta:.1f} s)"}
+
+
+def cpu_baseline_single_core(sc, n_sensors_sample=36, seed=0):
+    """The oracle on one host core, on a sensor sample of the same workload
+    (the multi-core figure above uses every core)."""
+    import oracle
+    cores = oracle.max_threads()
+    rng = np.random.default_rng(seed)
+    pick = np.sort(rng.choice(sc.n_sensors, n_sensors_sample, replace=False))
+    g = rng.standard_normal((1, len(pick), sc.n_samples)).astype(np.float32)
+    t0 = time.perf_counter()
+    _, n = oracle.forward(sc.balls, sc.sensors[:, pick], sc.c, sc.fs, sc.t0, sc.n_samples, sc.kappa, nthreads=1)
+    oracle.adjoint_state(sc.balls, sc.sensors[:, pick], sc.c, sc.fs, sc.t0, sc.n_samples, sc.kappa, g, nthreads=1)
+    dt = time.perf_counter() - t0
+    # the thread count set above persists in the oracle library: put it back
+    oracle.forward(sc.balls[:, :4], sc.sensors[:, :1], sc.c, sc.fs, sc.t0, sc.n_samples, sc.kappa, nthreads=cores)
+    return {"value": n / dt, "unit": UNIT, "cores": 1, "kind": "oracle",
+            "sample": f"{sc.name}: all {sc.n_balls} balls x {len(pick)} of {sc.n_sensors} sensors x "
+                      f"{sc.n_samples} samples, forward + adjoint in FP64 ({n} contributions, {dt:.1f} s)"}
 
 
 def run_reference(args):
@@ -363,6 +384,7 @@ def run_ours(args):
     ir_quality = None
     if args.ir_quality_iters > 0 and not args.no_4d:
         ir_quality = bench_ir_quality(args, pa, pa_inputs, dev)
+    large4d = bench_large4d(args, pa, pa_inputs, dev) if args.large4d else None
     clocks = sampler.stop()
 
     fwd_avg = statistics.mean(t_fwd)
@@ -402,8 +424,11 @@ def run_ours(args):
         line["imaging"] = imaging
     if ir_quality is not None:
         line["ir_quality"] = ir_quality
+    if large4d is not None:
+        line["large4d"] = large4d
     if rank == 0 and world == 1 and not args.no_cpu:
         line["cpu_baseline"] = cpu_baseline(sc)
+        line["cpu_baseline_single_core"] = cpu_baseline_single_core(sc)
     if rank == 0:
         print(json.dumps(line))
     return 0
@@ -511,6 +536,45 @@ def bench_imaging(args, pa, pa_inputs, dev, flush):
     out["ubp_vs_gt_map_ssim"] = {k: float(pa.ssim(u, g, minmax=True)) for k, u, g in zip(("xy", "yz", "xz"), mu, mg)}
     pa.device_error()
     return out
+
+
+def bench_large4d(args, pa, pa_inputs, dev):
+    """The paper's large-scale case: one 4D IR iteration (deform, forward, FP64
+    loss, adjoint, chain rule, Adam) over 1,000,000 balls x 50 frames with
+    1,024 sensors and 4,096 samples (4d-1m-50f), replayed from one CUDA graph
+    after a warm-up and the capture; L2 is not flushed (the iteration moves
+    ~20 GB)."""
+    import torch
+    from paper_2412_03898_gb300.ir import GGBallIR, init_deformation
+    sc = pa_inputs.config_scene(4)
+    n, F = sc.n_balls, sc.n_frames
+    to_dev = lambda a: pa.pad_last(torch.from_numpy(np.ascontiguousarray(a, dtype=np.float32)).to(dev))
+    geom = pa.Geometry(torch.from_numpy(sc.sensors).to(dev), sc.c, sc.fs, sc.t0, sc.n_samples, sc.kappa)
+    # ground-truth motion (radial pulsation and drift), generated here: the
+    # workload stores no frames
+    gt = to_dev(pa_inputs.gt_motion_frames(sc.balls, sc.axis, F)).contiguous()
+    meas = pa.forward(geom, gt, n)
+    C = pa.count_contributions(geom, gt, n)
+    del gt
+    t = torch.from_numpy(pa_inputs.frame_times(F)).to(dev)
+    canon = to_dev(sc.balls).contiguous()
+    ir = GGBallIR(geom, canon, init_deformation(65, canon.shape[-1], dev), t, meas, n)
+    ir.step()
+    ir.capture()
+    torch.cuda.synchronize()
+    ev = [torch.cuda.Event(enable_timing=True) for _ in range(2)]
+    iters = 2
+    ev[0].record()
+    for _ in range(iters):
+        ir.step_graph()
+    ev[1].record()
+    ev[1].synchronize()
+    pa.device_error()
+    s_per_iter = ev[0].elapsed_time(ev[1]) * 1e-3 / iters
+    return {"workload": f"{sc.name}: {n} balls, {F} frames, Nb = 65, {geom.n_sensors} sensors, {geom.n_samples} "
+                        "samples", "contributions_per_forward": C, "seconds_per_iteration": s_per_iter,
+            "contrib_per_s": 2 * C / s_per_iter, "iterations_timed": iters,
+            "device_memory_gb": torch.cuda.max_memory_allocated(dev) / 1e9}
 
 
 def bench_ir_quality(args, pa, pa_inputs, dev):

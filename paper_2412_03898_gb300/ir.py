@@ -191,10 +191,18 @@ class GGBallIR:
 
 def init_deformation(n_basis: int, stride: int, device, omega_scale: float = 0.0, seed: int = 0) -> torch.Tensor:
     """Deformation parameters [3, 5, Nb, stride]: omega (zero, or small random
-    weights), theta evenly spaced on [0, 1], sigma = 1/Nb."""
-    g = torch.Generator(device="cpu").manual_seed(seed)
-    d = torch.empty(3, 5, n_basis, stride, dtype=torch.float32)
-    d[0] = torch.randn(5, n_basis, stride, generator=g) * omega_scale / math.sqrt(max(n_basis, 1))
-    d[1] = torch.linspace(0.0, 1.0, n_basis).view(1, n_basis, 1) if n_basis > 1 else 0.0
-    d[2] = 1.0 / n_basis
-    return d.to(device)
+    weights drawn from a seeded CPU generator), theta evenly spaced on [0, 1],
+    sigma = 1/Nb.  Built on `device` (only random omega passes through host
+    memory)."""
+    d = torch.empty(3, 5, n_basis, stride, dtype=torch.float32, device=device)
+    if omega_scale != 0.0:
+        g = torch.Generator(device="cpu").manual_seed(seed)
+        d[0] = (torch.randn(5, n_basis, stride, generator=g) * omega_scale / math.sqrt(max(n_basis, 1))).to(device)
+    else:
+        d[0].zero_()
+    if n_basis > 1:
+        d[1] = torch.linspace(0.0, 1.0, n_basis, device=device).view(1, n_basis, 1)
+    else:
+        d[1].zero_()
+    d[2].fill_(1.0 / n_basis)
+    return d
