@@ -376,7 +376,6 @@ cudaError_t launch_gridstride(K kern, const AdjArgs &a, size_t smem, int sms, cu
 
 cudaError_t launch_adjoint_static(const AdjArgs &a, int sms, cudaStream_t st) {
   if (a.n_items == 0) return cudaSuccess;
-  // 4 pairs per group measured fastest on the static 100k-ball workload (2 and 8 slower)
   return launch_gridstride(k_adjoint_static, a, adj_static_smem(a.q.S), sms, st);
 }
 
@@ -396,7 +395,23 @@ cudaError_t launch_adjoint_batched(const BatchAdjArgs &a, int sms, cudaStream_t 
 
 cudaError_t launch_adjoint_4d(const AdjArgs &a, int sms, cudaStream_t st) {
   if (a.n_items == 0) return cudaSuccess;
-  return launch_gridstride(k_adjoint_4d, a, adj_4d_smem(a.q.S, a.nb), sms, st);
+  // Each warp takes its ball through every frame of a launch, so all of the
+  // launch's residual frames are live in L2 at once.  Launch over chunks of
+  // at most ~32 MB of [S][T] residuals (the 126 MB L2 then holds them), the
+  // chunks after the first accumulating into the outputs.
+  const long long frame_bytes = std::max(1LL, (long long)a.q.S * a.q.T * (long long)sizeof(float));
+  const int fc = (int)std::max(1LL, std::min<long long>(a.F, (32LL << 20) / frame_bytes));
+  for (int f0 = 0; f0 < a.F; f0 += fc) {
+    AdjArgs c = a;
+    c.F = std::min(fc, a.F - f0);
+    c.t_frames = a.t_frames + f0;
+    c.g = a.g + (long long)f0 * a.q.S * a.q.T;
+    c.frame_scale = a.frame_scale ? a.frame_scale + f0 : nullptr;
+    if (f0 > 0) c.flags |= PA_ACCUMULATE;
+    cudaError_t e = launch_gridstride(k_adjoint_4d, c, adj_4d_smem(a.q.S, a.nb), sms, st);
+    if (e != cudaSuccess) return e;
+  }
+  return cudaSuccess;
 }
 
 }  // namespace pa
