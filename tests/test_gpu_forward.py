@@ -170,3 +170,24 @@ def test_forward_full_size_sampled_sensors(pa):
     y_o, _ = oracle.forward(sc.balls, sc.sensors[:, pick], sc.c, sc.fs, sc.t0, sc.n_samples, sc.kappa)
     got = y[0, pick].cpu().numpy()
     assert rel_l2(got, y_o[0]) <= TRACE_TOL
+
+
+@pytest.mark.parametrize("tiles", [None, (8, 256, 128, 3, 4), (16, 1536, 512, 0, 8), (1, 1028, 4, 7, 2)])
+def test_forward_plan_and_workspace_size_are_consistent(pa, tiles):
+    sc = pa_inputs.small_scene(seed=1, n_balls=1003, n_sensors=37, n_samples=1028, n_frames=3)
+    geom = geometry(sc)
+    state = dev_pad(sc.frames)
+    F, S, T = 3, sc.n_sensors, sc.n_samples
+    p = pa.forward_plan(geom, state, sc.n_balls, tiles=tiles)
+    n_st, n_tt = -(-S // p["s_tile"]), -(-T // p["t_tile"])
+    assert p["ctas"] == F * n_st * n_tt * p["n_splits"]
+    assert p["t_tile"] % 4 == 0 and p["nb_tile"] % 4 == 0 and 1 <= p["s_tile"] <= 16
+    assert p["group"] in (1, 2, 4, 8, 16)
+    assert p["smem"] <= torch.cuda.get_device_properties(0).shared_memory_per_block_optin
+    if tiles is not None:
+        assert (p["s_tile"], p["t_tile"], p["nb_tile"]) == tuple(min(v, lim) for v, lim in zip(tiles[:3], (16, T, 1 << 30)))
+    ws = pa.forward_workspace_size(geom, state, sc.n_balls, tiles=tiles)
+    assert ws == (4 * p["n_splits"] * F * S * T if p["n_splits"] > 1 else 0)
+    # the ssim workspace covers its partials
+    assert pa._LIB.pa_ssim_workspace_size(64, 80) >= 8 * ((54 + 15) // 16) * ((70 + 15) // 16)
+    assert pa._LIB.pa_ssim_workspace_size(10, 80) == 0
