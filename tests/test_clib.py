@@ -64,3 +64,41 @@ def test_invalid_loss_and_adam_args_rejected_on_host(lib):
     assert lib.pa_residual_loss(None, None, 6, 1, None, None, None, None, 0, None) == _lib.PA_ERR_INVALID_ARG
     assert lib.pa_adam_step(None, None, None, None, 8, 1e-3, 0.9, 0.999, 1e-8, 0, None) == _lib.PA_ERR_INVALID_ARG
     assert lib.pa_loss_workspace_size(0, 1) == 0
+
+
+def test_imaging_and_chain_rule_args_rejected_on_host(lib):
+    from paper_2412_03898_gb300 import _lib
+    E = _lib.PA_ERR_INVALID_ARG
+    P = ctypes.c_void_p
+    fake = P(256)  # never dereferenced: every call below fails its host-side checks first
+    # pa_ubp_filter: fewer than 2 samples, aliasing, non-positive fs
+    assert lib.pa_ubp_filter(fake, 3, 1, 40.0, 0.0, P(512), None) == E
+    assert lib.pa_ubp_filter(fake, 3, 64, 40.0, 0.0, fake, None) == E
+    assert lib.pa_ubp_filter(fake, 3, 64, 0.0, 0.0, P(512), None) == E
+    # pa_ubp / pa_splat / pa_map: bad grids, NULL buffers, non-positive kappa
+    g = _lib.pa_geom(16, 4, 4, 1.5, 40.0, 0.0, 64, 5.0)
+    good = _lib.pa_grid((ctypes.c_float * 3)(0, 0, 0), 0.5, 4, 4, 4)
+    flat = _lib.pa_grid((ctypes.c_float * 3)(0, 0, 0), 0.0, 4, 4, 4)
+    empty = _lib.pa_grid((ctypes.c_float * 3)(0, 0, 0), 0.5, 0, 4, 4)
+    c3 = (ctypes.c_float * 3)(0, 0, 0)
+    assert lib.pa_ubp(ctypes.byref(g), c3, fake, ctypes.byref(flat), fake, None) == E
+    assert lib.pa_ubp(ctypes.byref(g), None, fake, ctypes.byref(good), fake, None) == E
+    assert lib.pa_ubp(ctypes.byref(g), c3, None, ctypes.byref(good), fake, None) == E
+    b = _lib.pa_balls(16, 4, 4)
+    assert lib.pa_splat(ctypes.byref(b), 0.0, ctypes.byref(good), fake, None) == E
+    assert lib.pa_splat(ctypes.byref(b), 5.0, ctypes.byref(empty), fake, None) == E
+    assert lib.pa_map(None, ctypes.byref(good), fake, fake, fake, None) == E
+    assert lib.pa_map(fake, ctypes.byref(flat), fake, fake, fake, None) == E
+    # pa_ssim: images smaller than the window, unknown flags
+    assert lib.pa_ssim_workspace_size(10, 80) == 0
+    assert lib.pa_ssim(fake, fake, 10, 80, 1.0, 0, None, fake, fake, 4096, None) == E
+    assert lib.pa_ssim(fake, fake, 64, 80, 1.0, 1 << 7, None, fake, fake, 4096, None) == E
+    assert lib.pa_ssim(fake, fake, 64, 80, 0.0, 0, None, fake, fake, 4096, None) == E
+    # pa_deform_backward: n_basis outside [1, 128], NULL gradient outputs, unknown flags
+    canon = _lib.pa_canon(16, 16, 16, 16, 4, 4, 129)
+    gr = _lib.pa_grads(16, 16, 16, 16)
+    assert lib.pa_deform_backward(ctypes.byref(canon), fake, 2, fake, ctypes.byref(gr), 0, None) == E
+    canon = _lib.pa_canon(16, 16, 16, 16, 4, 4, 65)
+    null_gr = _lib.pa_grads(16, None, 16, 16)
+    assert lib.pa_deform_backward(ctypes.byref(canon), fake, 2, fake, ctypes.byref(null_gr), 0, None) == E
+    assert lib.pa_deform_backward(ctypes.byref(canon), fake, 2, fake, ctypes.byref(gr), 1 << 5, None) == E
