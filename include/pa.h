@@ -374,6 +374,14 @@ PA_API size_t pa_ssim_workspace_size(int32_t H, int32_t W);
 PA_API int32_t pa_ssim(const float *x, const float *y, int32_t H, int32_t W, float L, uint32_t flags, float *map,
                        double *mean, void *workspace, size_t workspace_bytes, void *stream);
 
+/* Self-test of failure detection (no counterpart in the paper): launches one
+ * block that waits for an mbarrier phase nothing completes, with the same
+ * bounded wait that guards every TMA stage of pa_forward, giving up after
+ * limit_ns (1e3 <= limit_ns <= 1e9).  The kernel records PA_ERR_TIMEOUT in the
+ * device error word (read it with pa_device_error) and exits with nothing in
+ * flight, so the context stays usable. */
+PA_API int32_t pa_selftest_bounded_wait(uint64_t limit_ns, void *stream);
+
 #ifdef __cplusplus
 }
 #endif

@@ -185,6 +185,12 @@ def deform_backward(canon: torch.Tensor, omega: torch.Tensor, theta: torch.Tenso
     return out
 
 
+def selftest_bounded_wait(limit_ns: int = 2_000_000) -> None:
+    """Make the bounded in-kernel wait run out (PA_ERR_TIMEOUT is then
+    reported by the next device_error())."""
+    _lib.check(_LIB.pa_selftest_bounded_wait(int(limit_ns), _stream()), "pa_selftest_bounded_wait")
+
+
 def _tiles(tiles: Optional[Sequence[int]]):
     if tiles is None:
         return None

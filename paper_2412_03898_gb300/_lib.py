@@ -110,6 +110,7 @@ def load() -> ctypes.CDLL:
         "pa_map": (i32, [P, ctypes.POINTER(pa_grid), P, P, P, P]),
         "pa_ssim_workspace_size": (sz, [i32, i32]),
         "pa_ssim": (i32, [P, P, i32, i32, f32, u32, P, P, P, sz, P]),
+        "pa_selftest_bounded_wait": (i32, [ctypes.c_uint64, P]),
     }
     for name, (res, args) in sig.items():
         fn = getattr(lib, name)
@@ -139,4 +140,4 @@ def exported_symbols() -> list[str]:
             "pa_batched_workspace_size", "pa_forward_batched", "pa_adjoint_batched",
             "pa_loss_workspace_size", "pa_residual_loss", "pa_residual_loss_noalloc", "pa_sumsq", "pa_count_contributions", "pa_adam_step",
             "pa_adam_step_scheduled", "pa_step_increment", "pa_ubp_filter", "pa_ubp", "pa_splat", "pa_map",
-            "pa_ssim_workspace_size", "pa_ssim"]
+            "pa_ssim_workspace_size", "pa_ssim", "pa_selftest_bounded_wait"]

@@ -626,4 +626,12 @@ int32_t pa_ssim(const float *x, const float *y, int32_t H, int32_t W, float L, u
   return cuda_status(pa::launch_ssim(a, mean, mm, static_cast<cudaStream_t>(stream)));
 }
 
+
+int32_t pa_selftest_bounded_wait(uint64_t limit_ns, void *stream) {
+  if (limit_ns < 1000ull || limit_ns > 1000000000ull) return PA_ERR_INVALID_ARG;
+  const DevInfo *d = dev_info();
+  if (!d) return PA_ERR_CUDA;
+  return cuda_status(pa::launch_selftest_wait(limit_ns, d->err, static_cast<cudaStream_t>(stream)));
+}
+
 }  // extern "C"

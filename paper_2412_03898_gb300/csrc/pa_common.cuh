@@ -145,12 +145,13 @@ __device__ __forceinline__ bool mbar_try_wait(uint64_t *bar, unsigned parity) {
 
 // Waits for phase `parity` of `bar` for at most WAIT_LIMIT_NS; false if it
 // ran out.
-__device__ __forceinline__ bool mbar_wait_bounded(uint64_t *bar, unsigned parity) {
+__device__ __forceinline__ bool mbar_wait_bounded(uint64_t *bar, unsigned parity,
+                                                  unsigned long long limit_ns = WAIT_LIMIT_NS) {
   if (mbar_try_wait(bar, parity)) return true;
   const unsigned long long start = global_ns();
   while (true) {
     if (mbar_try_wait(bar, parity)) return true;
-    if (global_ns() - start > WAIT_LIMIT_NS) return false;
+    if (global_ns() - start > limit_ns) return false;
   }
 }
 

@@ -153,6 +153,7 @@ int ssim_blocks(int H, int W);
 int minmax_partials();
 cudaError_t launch_ssim(const SsimArgs &a, double *out, float4 *minmax_ws, cudaStream_t st);
 
+cudaError_t launch_selftest_wait(unsigned long long limit_ns, unsigned *err, cudaStream_t st);
 cudaError_t launch_deform_backward(const float *canon, const float *omega, const float *theta, const float *sigma,
                                    long long n, long long stride, int nb, const float *t, int F, const float *gstate,
                                    float *g_canon, float *g_omega, float *g_theta, float *g_sigma, bool acc,

@@ -123,6 +123,20 @@ __global__ void __launch_bounds__(256) k_deform_backward(const float *__restrict
   if (dom) set_error(err, PA_ERR_DOMAIN);
 }
 
+// Self-test of the bounded mbarrier wait that guards every TMA stage: one
+// thread waits for a phase of an mbarrier that nothing completes; the wait
+// gives up after limit_ns and records PA_ERR_TIMEOUT, as the forward does
+// when a copy never lands.  Nothing is in flight when the block exits.
+__global__ void k_selftest_wait(unsigned long long limit_ns, unsigned *err) {
+  __shared__ uint64_t bar;
+  if (threadIdx.x == 0) {
+    mbar_init(&bar, 1);
+    fence_barrier_init();
+  }
+  __syncthreads();
+  if (threadIdx.x == 0 && !mbar_wait_bounded(&bar, 0u, limit_ns)) set_error(err, PA_ERR_TIMEOUT);
+}
+
 // Per-frame partial sums of squared residuals in FP64 (each float4 is summed
 // in fp32 then promoted), optional residual 2 scale (pred - meas).
 __global__ void __launch_bounds__(256) k_loss_partial(const float4 *__restrict__ pred, const float4 *__restrict__ meas,
@@ -255,6 +269,11 @@ cudaError_t launch_deform_backward(const float *canon, const float *omega, const
   const long long blocks = std::min<long long>((total + 255) / 256, 152LL * 32);
   k_deform_backward<<<(unsigned)blocks, 256, 0, st>>>(canon, omega, theta, sigma, n, stride, nb, t, F, gstate,
                                                       g_canon, g_omega, g_theta, g_sigma, acc, err);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_selftest_wait(unsigned long long limit_ns, unsigned *err, cudaStream_t st) {
+  k_selftest_wait<<<1, 32, 0, st>>>(limit_ns, err);
   return cudaGetLastError();
 }
 
