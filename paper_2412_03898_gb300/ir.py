@@ -179,6 +179,27 @@ class GGBallIR:
         self._adam()
         return self.loss
 
+    # -- checkpoint / resume -----------------------------------------------------
+    def state_dict(self) -> dict:
+        """Everything an iteration reads and updates: parameters, Adam moments and
+        the step number (device tensors are copied to host memory)."""
+        return {"canon": self.canon.cpu(), "deform": self.deform.cpu(), "m_canon": self.m_canon.cpu(),
+                "v_canon": self.v_canon.cpu(), "m_deform": self.m_deform.cpu(), "v_deform": self.v_deform.cpu(),
+                "step": int(self.step_count), "n": int(self.n), "lr_scale": self.lr_scale}
+
+    def load_state_dict(self, sd: dict) -> None:
+        """Resume from state_dict(); the next iteration continues the schedule
+        exactly (bitwise, for the same measurements and launch configuration).
+        A captured graph keeps pointing at these same buffers."""
+        if int(sd["n"]) != self.n or tuple(sd["canon"].shape) != tuple(self.canon.shape) or \
+                tuple(sd["deform"].shape) != tuple(self.deform.shape):
+            raise ValueError("checkpoint does not match this problem's shapes")
+        for name in ("canon", "deform", "m_canon", "v_canon", "m_deform", "v_deform"):
+            getattr(self, name).copy_(sd[name])
+        self.step_count = int(sd["step"])
+        self.step_dev.fill_(self.step_count)
+        self.lr_scale = float(sd.get("lr_scale", self.lr_scale))
+
     def launches_per_step(self, per_frame: bool = False) -> int:
         from . import forward_plan
         p = forward_plan(self.geom, self.state[:1] if per_frame else self.state, self.n)

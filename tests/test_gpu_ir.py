@@ -99,3 +99,27 @@ def test_ir_loss_decreases(pa):
     for _ in range(20):
         last = float(ir.step_graph().sum())
     assert last < first
+
+
+def test_checkpoint_resume_is_bitwise(pa, tmp_path):
+    from paper_2412_03898_gb300.ir import GGBallIR
+    geom, canon, deform, t, meas, n = _problem(pa, seed=7)
+    a = GGBallIR(geom, canon.clone(), deform.clone(), t, meas, n)
+    for _ in range(3):
+        a.step()
+    path = tmp_path / "ir.pt"
+    torch.save(a.state_dict(), path)
+    for _ in range(2):
+        a.step()
+    b = GGBallIR(geom, canon.clone(), deform.clone(), t, meas, n)
+    b.load_state_dict(torch.load(path))
+    assert b.step_count == 3 and int(b.step_dev.item()) == 3
+    b.capture()  # the warm-up inside capture is iteration 4; replay is iteration 5
+    b.step_graph()
+    torch.cuda.synchronize()
+    assert a.step_count == b.step_count == 5
+    assert torch.equal(a.canon, b.canon) and torch.equal(a.deform, b.deform)
+    assert torch.equal(a.m_deform, b.m_deform) and torch.equal(a.v_canon, b.v_canon)
+    with pytest.raises(ValueError):
+        c = GGBallIR(geom, canon[:, :-4].clone(), deform[..., :-4].clone(), t, meas, n - 4)
+        c.load_state_dict(torch.load(path))
