@@ -425,25 +425,38 @@ class PAProject(torch.autograd.Function):
 
 
 class PAProject4D(torch.autograd.Function):
-    """(canon, omega, theta, sigma) -> traces [F, S, T] through Eq. 1-2.  The
-    per-frame states live only for the forward call; backward recomputes them
-    inside the adjoint kernel."""
+    """(canon, omega, theta, sigma) -> traces [F, S, T] through Eq. 1-2.
+
+    By default the per-frame states of the forward call are kept (20 bytes
+    per ball and frame, small beside the deformation parameters' 3.9 KB per
+    ball) and backward runs the static adjoint over them followed by
+    deform_backward, the faster form.  keep_states=False drops them and
+    backward runs the fused 4D adjoint, which recomputes them in-kernel."""
 
     @staticmethod
-    def forward(ctx, canon, omega, theta, sigma, geom: Geometry, t_frames, n: Optional[int] = None):
+    def forward(ctx, canon, omega, theta, sigma, geom: Geometry, t_frames, n: Optional[int] = None,
+                keep_states: bool = True):
         state = deform_balls(canon, omega, theta, sigma, t_frames, n)
         traces = forward(geom, state, n)
-        del state
-        ctx.geom, ctx.n = geom, n
-        ctx.save_for_backward(canon, omega, theta, sigma, t_frames)
+        ctx.geom, ctx.n, ctx.keep = geom, n, keep_states
+        if keep_states:
+            ctx.save_for_backward(canon, omega, theta, sigma, t_frames, state)
+        else:
+            del state
+            ctx.save_for_backward(canon, omega, theta, sigma, t_frames)
         return traces
 
     @staticmethod
     def backward(ctx, g):
-        canon, omega, theta, sigma, t_frames = ctx.saved_tensors
-        gc, go, gt, gs = adjoint(ctx.geom, g.contiguous(), canon=canon, omega=omega, theta=theta, sigma=sigma,
-                                 t_frames=t_frames, n=ctx.n)
-        return gc, go, gt, gs, None, None, None
+        if ctx.keep:
+            canon, omega, theta, sigma, t_frames, state = ctx.saved_tensors
+            g_state = adjoint(ctx.geom, g.contiguous(), state=state, n=ctx.n)
+            gc, go, gt, gs = deform_backward(canon, omega, theta, sigma, t_frames, g_state, ctx.n)
+        else:
+            canon, omega, theta, sigma, t_frames = ctx.saved_tensors
+            gc, go, gt, gs = adjoint(ctx.geom, g.contiguous(), canon=canon, omega=omega, theta=theta, sigma=sigma,
+                                     t_frames=t_frames, n=ctx.n)
+        return gc, go, gt, gs, None, None, None, None
 
 
 class PALoss(torch.autograd.Function):

@@ -141,14 +141,15 @@ def test_autograd_functions(pa):
         assert rel_l2(got[:, ch], g_o[:, ch]) <= GRAD_TOL
 
 
-def test_autograd_4d_recomputes_states(pa):
+@pytest.mark.parametrize("keep_states", [True, False])  # static adjoint + chain rule, or the fused 4D adjoint
+def test_autograd_4d(pa, keep_states):
     rng = np.random.default_rng(61)
     n, nb, F = 120, 8, 4
     sc = pa_inputs.small_scene(seed=61, n_balls=n, n_sensors=12, n_samples=512)
     om, th, sg = pa_inputs.random_deform(n, nb, rng)
     t = torch.from_numpy(pa_inputs.frame_times(F)).cuda()
     params = [dev_pad(x).requires_grad_(True) for x in (sc.balls, om, th, sg)]
-    y = pa.PAProject4D.apply(*params, geometry(sc), t, n)
+    y = pa.PAProject4D.apply(*params, geometry(sc), t, n, keep_states)
     # a random upstream gradient: a constant one makes every true gradient a
     # near-cancelling sum (~1e-6 of its terms), which no FP32 path resolves
     up = rng.standard_normal(tuple(y.shape)).astype(np.float32)
