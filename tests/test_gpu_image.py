@@ -167,3 +167,27 @@ def test_imaging_edge_cases(pa):
     x, y = rng.random((11, 11)).astype(np.float32), rng.random((11, 11)).astype(np.float32)
     got = float(pa.ssim(torch.from_numpy(x).cuda(), torch.from_numpy(y).cuda()))
     assert abs(got - oracle.ssim(x, y)) <= 1e-5
+
+
+@pytest.mark.slow
+def test_full_size_heart_sampled_lines(pa):
+    """The bench's imaging workload (simulated heart frame 0, 1,024 sensors,
+    UBP and splat onto 256^3 voxels of 0.2 mm), checked on three sampled voxel
+    lines along x that the oracle computes one by one."""
+    sc = pa_inputs.heart_phantom()
+    n = sc.n_balls
+    st = dev_pad(sc.frames[0])
+    geom = pa.Geometry(torch.from_numpy(sc.sensors).cuda(), sc.c, sc.fs, sc.t0, sc.n_samples, sc.kappa)
+    y = pa.forward(geom, st[None], n)[0].contiguous()
+    b = pa.ubp_filter(y, sc.fs, sc.t0)
+    grid = pa.Grid.cube(25.6, 256)
+    vol = pa.ubp(geom, b, grid).cpu().numpy()
+    gt = pa.splat(st, grid, sc.kappa, n).cpu().numpy()
+    pa.device_error()
+    b_h = b.cpu().numpy()
+    for iz, iy in ((128, 128), (120, 140), (131, 97)):
+        origin = np.array([grid.origin[0], grid.origin[1] + grid.h * iy, grid.origin[2] + grid.h * iz])
+        line_u = oracle.ubp(b_h, sc.sensors, np.zeros(3), sc.c, sc.fs, sc.t0, origin, grid.h, (1, 1, 256))[0, 0]
+        assert rel_l2(vol[iz, iy], line_u) <= UBP_TOL, (iz, iy)
+        line_s = oracle.splat(sc.frames[0], sc.kappa, origin, grid.h, (1, 1, 256))[0, 0]
+        assert rel_l2(gt[iz, iy], line_s) <= SPLAT_TOL, (iz, iy)

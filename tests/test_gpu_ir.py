@@ -123,3 +123,34 @@ def test_checkpoint_resume_is_bitwise(pa, tmp_path):
     with pytest.raises(ValueError):
         c = GGBallIR(geom, canon[:, :-4].clone(), deform[..., :-4].clone(), t, meas, n - 4)
         c.load_state_dict(torch.load(path))
+
+
+def test_ir_recovers_motion(pa):
+    """40 IR iterations on a small 4D problem (ground-truth radial pulsation
+    and drift, canonical cloud = frame 0) lower the loss and the RMS position
+    error of the deformed cloud against the ground-truth frames."""
+    from paper_2412_03898_gb300.ir import GGBallIR
+    sc = pa_inputs.small_scene(seed=12, n_balls=400, n_sensors=48, n_samples=1024, n_frames=5)
+    n = sc.n_balls
+    geom = geometry(sc)
+    gt = dev_pad(sc.frames)
+    meas = pa.forward(geom, gt, n)
+    from paper_2412_03898_gb300.ir import init_deformation
+    canon = dev_pad(sc.frames[0])
+    t = torch.from_numpy(pa_inputs.frame_times(5)).cuda()
+    ir = GGBallIR(geom, canon, init_deformation(8, canon.shape[-1], "cuda"), t, meas, n, lr_scale=10.0)
+
+    def rmse():
+        st = pa.deform_balls(ir.canon, ir.deform[0], ir.deform[1], ir.deform[2], t, n)
+        return float((st[:, :3, :n] - gt[:, :3, :n]).pow(2).sum(1).mean().sqrt())
+
+    e0 = rmse()
+    l0 = float(ir.step().sum())
+    for _ in range(39):
+        ir.step()
+    l1 = float(ir.loss.sum())
+    e1 = rmse()
+    print(f"loss {l0:.4g} -> {l1:.4g}, rmse {e0:.4g} -> {e1:.4g} mm")
+    # measured: loss 3.32 -> 1.10, RMS error 0.288 -> 0.249 mm
+    assert l1 < 0.5 * l0
+    assert e1 < 0.95 * e0
