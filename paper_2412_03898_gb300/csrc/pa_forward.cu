@@ -31,6 +31,7 @@ namespace pa {
 namespace {
 
 constexpr int kMaxThreads = 512;  // at most 16 sensors (warps) per CTA
+constexpr long long kMaxBallsPerSplit = 131072;  // default plans split larger ball sets
 
 // Shared-memory layout of a forward CTA.
 struct FwdSmem {
@@ -532,6 +533,11 @@ FwdPlan forward_plan(int S, int T, long long n, int F, int sms, int s_tile_o, in
       if (sp >= max_splits) break;
     }
   }
+  // Smaller ball ranges have tighter bounding boxes, hence narrower arrival
+  // bands and fewer culled chunks per CTA: at least one split per
+  // kMaxBallsPerSplit balls (on 1e6 balls x 50 frames x 1024 sensors:
+  // 1 split 4.01 s, 2 splits 3.48 s, 8 splits 3.20 s).
+  if (splits_o <= 0) splits = std::max(splits, (n + kMaxBallsPerSplit - 1) / kMaxBallsPerSplit);
   splits = std::max(1LL, std::min(splits, max_splits));
   // balls per split: multiple of 4 so every TMA source stays 16-byte aligned
   long long bps = (n + splits - 1) / splits;
