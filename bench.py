@@ -5,9 +5,12 @@ second of one forward + FP64 loss/residual + adjoint step on the static
 100k-ball workload (vessel tree in a 30 mm cube, 576 sensors on a 55 mm
 hemisphere, 4096 samples at 40 MHz), inputs resident in HBM, L2 flushed
 before every timed step.  Extra keys: end-to-end through host buffers, the
-dominant kernel's roofline, the FP64 oracle timed on the host cores, and
-4D IR iterations/s (100k balls x 20 frames) batched in a CUDA graph vs plain
-per-frame launches.
+dominant kernel's roofline, the FP64 oracle timed on the host cores, 4D IR
+iterations/s (100k balls x 20 frames) batched in a CUDA graph vs plain
+per-frame launches, 16 uneven scenes in persistent launches, the imaging
+tools (UBP, splat, MAP, SSIM) on the simulated heart, and the 4D
+reconstruction quality against ground truth next to UBP; --large4d adds one
+IR iteration on 1M balls x 50 frames.
 
   python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
 
