@@ -144,7 +144,9 @@ typedef struct pa_grid {
 /* Human-readable name of a status code (static storage). */
 PA_API const char *pa_status_string(int32_t status);
 
-/* Library ABI version (major*100 + minor). */
+/* Library ABI version (major*100 + minor).  1.01 added pa_deform_backward,
+ * the imaging calls (pa_ubp_filter, pa_ubp, pa_splat, pa_map, pa_ssim*) and
+ * pa_selftest_bounded_wait; every 1.00 call is unchanged. */
 PA_API int32_t pa_version(void);
 
 /* Reads, returns in *out (host) and clears the device error word of the
