@@ -94,6 +94,8 @@ def parse():
     ap.add_argument("--no-imaging", action="store_true", help="skip the UBP / splat / MAP / SSIM leg")
     ap.add_argument("--large4d", action="store_true",
                     help="add the 1M-ball, 50-frame IR iteration (4d-1m-50f; ~20 GB of device memory)")
+    ap.add_argument("--heart-ir", type=int, default=0, metavar="ITERS",
+                    help="add the simulated-heart 4D reconstruction (Sec. 3.1) with this many IR iterations")
     ap.add_argument("--ir-quality-iters", type=int, default=160,
                     help="IR iterations of the 4D reconstruction-quality leg (0 = skip)")
     a = ap.parse_args()
@@ -388,6 +390,7 @@ def run_ours(args):
     if args.ir_quality_iters > 0 and not args.no_4d:
         ir_quality = bench_ir_quality(args, pa, pa_inputs, dev)
     large4d = bench_large4d(args, pa, pa_inputs, dev) if args.large4d else None
+    heart_ir = bench_heart_ir(args, pa, pa_inputs, dev) if args.heart_ir > 0 else None
     clocks = sampler.stop()
 
     fwd_avg = statistics.mean(t_fwd)
@@ -429,6 +432,8 @@ def run_ours(args):
         line["ir_quality"] = ir_quality
     if large4d is not None:
         line["large4d"] = large4d
+    if heart_ir is not None:
+        line["heart_ir"] = heart_ir
     if rank == 0 and world == 1 and not args.no_cpu:
         line["cpu_baseline"] = cpu_baseline(sc)
         line["cpu_baseline_single_core"] = cpu_baseline_single_core(sc)
@@ -539,6 +544,65 @@ def bench_imaging(args, pa, pa_inputs, dev, flush):
     out["ubp_vs_gt_map_ssim"] = {k: float(pa.ssim(u, g, minmax=True)) for k, u, g in zip(("xy", "yz", "xz"), mu, mg)}
     pa.device_error()
     return out
+
+
+def bench_heart_ir(args, pa, pa_inputs, dev):
+    """The paper's first simulation (Sec. 3.1) on synthetic data: the 17-frame
+    simulated heart seen by 1,024 sensors on a 60 mm sphere, reconstructed by
+    the 4D IR loop from the ground-truth frame 0 with zero deformation, and by
+    UBP frame by frame; XY / YZ / XZ MAP-SSIM against the splatted ground truth
+    at the first, middle and last frames (Fig. 5-7)."""
+    import torch
+    from paper_2412_03898_gb300.ir import GGBallIR, init_deformation
+    sc = pa_inputs.heart_phantom()
+    n, F = sc.n_balls, sc.n_frames
+    to_dev = lambda a: pa.pad_last(torch.from_numpy(np.ascontiguousarray(a, dtype=np.float32)).to(dev))
+    geom = pa.Geometry(torch.from_numpy(sc.sensors).to(dev), sc.c, sc.fs, sc.t0, sc.n_samples, sc.kappa)
+    gt = to_dev(sc.frames).contiguous()
+    meas = pa.forward(geom, gt, n)
+    t = torch.from_numpy(pa_inputs.frame_times(F)).to(dev)
+    ir = GGBallIR(geom, to_dev(sc.frames[0]).contiguous(), init_deformation(65, gt.shape[-1], dev), t, meas, n)
+    grid = pa.Grid.cube(25.6, 256)
+    frames = [0, F // 2, F - 1]
+    vol = torch.empty(grid.shape, dtype=torch.float32, device=dev)
+    bfilt = torch.empty(geom.n_sensors, geom.n_samples, dtype=torch.float32, device=dev)
+    gt_m = {}
+    for f in frames:
+        pa.splat(gt[f], grid, sc.kappa, n, out=vol)
+        gt_m[f] = [m.clone() for m in pa.maps(vol, grid)]
+
+    def ssim_model():
+        state = pa.deform_balls(ir.canon, ir.deform[0], ir.deform[1], ir.deform[2], t, n)
+        out = {}
+        for f in frames:
+            pa.splat(state[f], grid, sc.kappa, n, out=vol)
+            out[f] = [float(pa.ssim(u, g, minmax=True)) for u, g in zip(pa.maps(vol, grid), gt_m[f])]
+        return out
+
+    before = ssim_model()
+    loss0 = float(ir.step().sum())
+    ir.capture()
+    ev = [torch.cuda.Event(enable_timing=True) for _ in range(2)]
+    ev[0].record()
+    for _ in range(args.heart_ir - 2):
+        ir.step_graph()
+    ev[1].record()
+    ev[1].synchronize()
+    loss1 = float(ir.loss.sum())
+    after = ssim_model()
+    ubp = {}
+    for f in frames:
+        pa.ubp_filter(meas[f], sc.fs, sc.t0, out=bfilt)
+        pa.ubp(geom, bfilt, grid, out=vol)
+        ubp[f] = [float(pa.ssim(u, g, minmax=True)) for u, g in zip(pa.maps(vol, grid), gt_m[f])]
+    pa.device_error()
+    views = ("xy", "yz", "xz")
+    fmt = lambda d: {f"frame{f + 1}": dict(zip(views, v)) for f, v in d.items()}
+    return {"workload": f"{sc.name}: {n} balls, {F} frames, Nb = 65, {geom.n_sensors} sensors; MAPs on "
+                        f"{grid.shape[0]}^3 x {grid.h:.2f} mm", "iterations": args.heart_ir,
+            "ms_per_iteration": ev[0].elapsed_time(ev[1]) / max(args.heart_ir - 2, 1),
+            "loss_first": loss0, "loss_last": loss1, "map_ssim_4d_before": fmt(before),
+            "map_ssim_4d_after": fmt(after), "map_ssim_ubp": fmt(ubp)}
 
 
 def bench_large4d(args, pa, pa_inputs, dev):
