@@ -112,9 +112,7 @@ def tune_batched(scenes, candidates: Optional[Sequence[tuple]] = None, reps: int
     smem_max = torch.cuda.get_device_properties(dev).shared_memory_per_block_optin
     cands = []
     for c in (candidates or DEFAULT_CANDIDATES):
-        s_tile, t_tile, nb = c[0], c[1], c[2]
-        smem = 128 + 4 * 2 * 5 * nb + 16 * 32 * s_tile + 8 * s_tile * t_tile
-        if smem <= smem_max:
+        if forward_plan(scenes[0].geom, scenes[0].state, scenes[0].n, tiles=c)["smem"] <= smem_max:
             cands.append(c)
     flush = torch.empty(64 * 1024 * 1024, dtype=torch.float32, device=dev)
     best, best_ms = None, float("inf")

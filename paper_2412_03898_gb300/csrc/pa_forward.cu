@@ -10,15 +10,19 @@
 //    into shared memory by TMA bulk copies (cp.async.bulk) completing on
 //    mbarriers, double buffered, issued by one thread.
 //  - Per 32-ball chunk, the 32 lanes compute the window and phase of 32
-//    (ball, sensor) pairs in parallel (double-float distance, once per pair)
-//    and publish them in shared memory.  The warp sorts the pairs by first
-//    sample (bitonic network on shuffles) and sweeps groups of G consecutive
-//    pairs over the union of their windows: each lane owns one sample of a
+//    (ball, sensor) pairs in parallel (double-float distance, once per pair).
+//    The warp sorts the pairs by first sample (bitonic network on shuffles);
+//    lane i then holds the i-th pair, and each group of G consecutive sorted
+//    pairs gets one shared-memory record with its first sample, its step
+//    count and every member's phase at that sample.  The warp sweeps each
+//    group over the union of its windows: each lane owns one sample of a
 //    32-sample step, adds the G balls' pulses to it in a register
 //        u -= 32 du;  v = amp u 2^(-u^2)  if |u| <= kappa K_S
 //    and does one shared-memory load and store per sample and group.  Sorted
 //    groups overlap almost completely, so the sweep wastes few lanes while
-//    giving G independent dependency chains per step.
+//    giving G independent dependency chains per step.  Trace rows carry 32
+//    samples of padding, so a group's last step needs no bound test (lanes
+//    past every window add an exact zero).
 //  - Trace tiles are flushed with coalesced float4 stores.  With more than
 //    one ball split, partial traces go to the workspace and a second kernel
 //    sums them in split order (deterministic).
@@ -33,24 +37,39 @@ namespace {
 constexpr int kMaxThreads = 512;  // at most 16 sensors (warps) per CTA
 constexpr long long kMaxBallsPerSplit = 131072;  // default plans split larger ball sets
 
+constexpr int kRowPad = 32;  // samples of padding after every trace row
+
 // Shared-memory layout of a forward CTA.
 struct FwdSmem {
   uint64_t *bars;  // 2 mbarriers (TMA stages)
   float *sball;    // [2][5][nb_tile] ball tiles
-  float4 *srec;    // [s_tile][32] pair records
-  float *str;      // [s_tile][t_tile] trace tiles (high part)
-  float *strlo;    // [s_tile][t_tile] rounding errors of str (compensated sum)
+  float *sgrp;     // [s_tile][128] group records of the current chunk
+  float *str;      // [s_tile][t_tile + kRowPad] trace tiles (high part)
+  float *strlo;    // [s_tile][t_tile + kRowPad] rounding errors of str (compensated sum)
 };
 
 __device__ __forceinline__ FwdSmem fwd_smem(unsigned char *raw, int s_tile, int t_tile, int nb_tile) {
   FwdSmem m;
   m.bars = reinterpret_cast<uint64_t *>(raw);
   m.sball = reinterpret_cast<float *>(raw + 128);
-  m.srec = reinterpret_cast<float4 *>(m.sball + 2 * 5 * nb_tile);
-  m.str = reinterpret_cast<float *>(m.srec + s_tile * 32);
-  m.strlo = m.str + s_tile * t_tile;
+  m.sgrp = m.sball + 2 * 5 * nb_tile;
+  m.str = m.sgrp + s_tile * 128;
+  m.strlo = m.str + s_tile * (t_tile + kRowPad);
   return m;
 }
+
+// Group records in a warp's 128-float area (16-byte aligned).  G >= 2: per
+// group, H = G/2 float4 (u_x, u_y, -du_x, -du_y) of ball pairs, H float2
+// (amp_x, amp_y), then (first sample, step count) as ints; stride rounded up
+// to 4 floats.  G = 1: one float4 (u, -du, amp, first | steps << 16) each.
+template <int G>
+__host__ __device__ constexpr int grp_stride() {
+  return G == 1 ? 4 : ((6 * (G / 2) + 2) + 3) & ~3;
+}
+static_assert(32 / 2 * grp_stride<2>() <= 128 && 32 / 4 * grp_stride<4>() <= 128 &&
+                  32 / 8 * grp_stride<8>() <= 128 && 32 / 16 * grp_stride<16>() <= 128 &&
+                  32 * grp_stride<1>() <= 128,
+              "group records exceed a warp's area");
 
 // One work item: frame state `state_f`, sensors [st*s_tile, +s_tile), samples
 // [k0, k0+klen), balls [b_begin, b_end).  Writes (or adds) the trace tile to
@@ -72,7 +91,7 @@ __device__ __forceinline__ bool forward_item(const Acq &q, const float *state_f,
 
   __syncthreads();  // the previous item (if any) is done with the trace tiles
   float4 *str4 = reinterpret_cast<float4 *>(m.str);
-  const int nz = 2 * s_tile * t_tile / 4;  // high and low parts
+  const int nz = 2 * s_tile * (t_tile + kRowPad) / 4;  // high and low parts, padding included
   for (int i = tid; i < nz; i += blockDim.x) str4[i] = make_float4(0.f, 0.f, 0.f, 0.f);
 
   auto issue = [&](int t) {
@@ -98,9 +117,11 @@ __device__ __forceinline__ bool forward_item(const Acq &q, const float *state_f,
     sy = q.sensors[q.sstride + s];
     sz = q.sensors[2 * q.sstride + s];
   }
-  float *mytr = m.str + warp * t_tile;
-  float *mylo = m.strlo + warp * t_tile;
-  float4 *myrec = m.srec + warp * 32;
+  float *mytr = m.str + warp * (t_tile + kRowPad);
+  float *mylo = m.strlo + warp * (t_tile + kRowPad);
+  float *mygrp = m.sgrp + warp * 128;
+  constexpr int H = (G + 1) / 2;  // ball pairs per group
+  constexpr int GS = grp_stride<G>();
   bool dom = false;
   // window bound in scaled units: |u| <= kappa K_S (Gaussian), |u| <= 1 (uniform)
   const float umax2 = UNIFORM ? 1.f : (q.kappa * K_S) * (q.kappa * K_S);
@@ -128,6 +149,7 @@ __device__ __forceinline__ bool forward_item(const Acq &q, const float *state_f,
         if (__ballot_sync(FULL, maybe) == 0) continue;
         PairWin w;
         w.W = 0;
+        w.u0 = w.du = w.amp = 0.f;
         w.domain_err = false;
         if (bi < cnt)
           w = pair_window<UNIFORM>(q, bx[bi], bx[nbt + bi], bx[2 * nbt + bi], bx[3 * nbt + bi],
@@ -136,83 +158,102 @@ __device__ __forceinline__ bool forward_item(const Acq &q, const float *state_f,
         const bool valid = w.W > 0;
         const int nv = __popc(__ballot_sync(FULL, valid));
         if (nv == 0) continue;
-        // every lane publishes a record; an invalid pair's record is a pad far
-        // outside every window with zero amplitude (kl = 0xffff, kend = 0, so
-        // it never widens a group's sample range)
-        myrec[lane] = valid ? make_float4(w.u0, w.du, w.amp, __int_as_float((w.klo - k0) | ((w.klo - k0 + w.W - 1) << 16)))
-                            : make_float4(1e30f, 0.f, 0.f, __int_as_float(0xffff));
         // sort by first sample; invalid pairs last; lane index in the low bits
         const unsigned key = warp_sort(((valid ? (unsigned)(w.klo - k0) : 0xffffu) << 5) | (unsigned)lane, lane);
+        // lane i takes the i-th pair in that order (positions >= nv are pads)
+        const int src = (int)(key & 31u);
+        const float pu0 = __shfl_sync(FULL, w.u0, src);
+        const float pdu = __shfl_sync(FULL, w.du, src);
+        const float pamp = __shfl_sync(FULL, w.amp, src);
+        const int pW = __shfl_sync(FULL, w.W, src);
+        const bool real = lane < nv;
+        const int kl = (int)(key >> 5);  // first sample relative to k0
+        // the group's first sample (sorted: its first member's) and last sample
+        const int kmin = __shfl_sync(FULL, kl, lane & ~(G - 1));
+        int kmax = real ? kl + pW - 1 : -1;
+#pragma unroll
+        for (int o = 1; o < G; o <<= 1) kmax = max(kmax, __shfl_xor_sync(FULL, kmax, o));
+        const int nsteps = ((kmax - kmin) >> 5) + 1;
+        // phase at the group's first sample: kmin - kl is a small exact
+        // integer; pads sit far outside every window with zero amplitude
+        const float us = real ? fmaf((float)(kmin - kl), -pdu, pu0) : 1e30f;
+        const float nd = real ? -pdu : 0.f;
+        const float am = real ? pamp : 0.f;
+        __syncwarp();  // the previous chunk's groups are done with the records
+        if (G == 1) {
+          reinterpret_cast<float4 *>(mygrp)[lane] = make_float4(us, nd, am, __int_as_float(kmin | (nsteps << 16)));
+        } else {
+          const int j = lane & (G - 1);
+          float *r = mygrp + (lane / G) * GS;
+          r[(j >> 1) * 4 + (j & 1)] = us;
+          r[(j >> 1) * 4 + 2 + (j & 1)] = nd;
+          r[4 * H + j] = am;
+          if (j == 0) reinterpret_cast<int2 *>(r + 6 * H)[0] = make_int2(kmin, nsteps);
+        }
         __syncwarp();
+        const float lf = (float)lane;
         for (int g0 = 0; g0 < nv; g0 += G) {
-          float uq[G], duq[G], aq[G];
-          int klq[G];
-          int kmin = 0xffff, kmax = -1;
-#pragma unroll
-          for (int q = 0; q < G; ++q) {
-            // positions past nv hold pads (sorted last)
-            const int src = (int)(__shfl_sync(FULL, key, (g0 + q) & 31) & 31u);
-            const float4 r = myrec[src];
-            const int pk = __float_as_int(r.w);
-            klq[q] = pk & 0xffff;
-            kmin = min(kmin, klq[q]);
-            kmax = max(kmax, pk >> 16);
-            uq[q] = r.x;
-            duq[q] = r.y;
-            aq[q] = r.z;
-          }
           // balls in twos: u, its step and amp*u of two balls share one packed
-          // FP32x2 instruction.  u starts at this lane's first sample
-          // kmin + lane; the offset from the pair's own first sample is a small
-          // exact integer (pads stay far outside every window).
-          float2 u2[(G + 1) / 2], nd2[(G + 1) / 2], amp2[(G + 1) / 2];
+          // FP32x2 instruction; u starts at this lane's first sample
+          float2 u2[H], nd2[H], amp2[H];
+          int kb, ns;
+          if (G == 1) {
+            const float4 r = reinterpret_cast<const float4 *>(mygrp)[g0];
+            u2[0] = make_float2(fmaf(lf, r.y, r.x), 1e30f);
+            nd2[0] = make_float2(32.f * r.y, 0.f);
+            amp2[0] = make_float2(r.z, 0.f);
+            kb = __float_as_int(r.w) & 0xffff;
+            ns = __float_as_int(r.w) >> 16;
+          } else {
+            const float *r = mygrp + (g0 / G) * GS;
 #pragma unroll
-          for (int h = 0; h < (G + 1) / 2; ++h) {
-            const int q0 = 2 * h, q1 = min(2 * h + 1, G - 1);
-            const bool has1 = 2 * h + 1 < G;
-            u2[h] = make_float2(fmaf((float)(kmin + lane - klq[q0]), -duq[q0], uq[q0]),
-                                has1 ? fmaf((float)(kmin + lane - klq[q1]), -duq[q1], uq[q1]) : 1e30f);
-            nd2[h] = make_float2(-32.f * duq[q0], has1 ? -32.f * duq[q1] : 0.f);
-            amp2[h] = make_float2(aq[q0], has1 ? aq[q1] : 0.f);
+            for (int h = 0; h < H; ++h) {
+              const float4 ud = reinterpret_cast<const float4 *>(r)[h];
+              const float2 ndh = make_float2(ud.z, ud.w);
+              u2[h] = __ffma2_rn(make_float2(lf, lf), ndh, make_float2(ud.x, ud.y));
+              nd2[h] = __fmul2_rn(make_float2(32.f, 32.f), ndh);
+              amp2[h] = reinterpret_cast<const float2 *>(r + 4 * H)[h];
+            }
+            const int2 kn = reinterpret_cast<const int2 *>(r + 6 * H)[0];
+            kb = kn.x;
+            ns = kn.y;
           }
-          for (int base = kmin; base <= kmax; base += 32) {
-            const int k = base + lane;
-            if (k <= kmax) {
-              // the group's pulses at this sample, summed in registers (one
-              // partial sum per ball pair keeps the dependency chains short)
-              float tp[(G + 1) / 2];
+          float *pt = mytr + kb + lane;
+          float *pl = mylo + kb + lane;
+          for (int it = 0; it < ns; ++it, pt += 32, pl += 32) {
+            // the group's pulses at this sample, summed in registers (one
+            // partial sum per ball pair keeps the dependency chains short)
+            float tp[H];
 #pragma unroll
-              for (int h = 0; h < (G + 1) / 2; ++h) {
-                const float2 sq = __fmul2_rn(u2[h], u2[h]);
-                const float2 w = __fmul2_rn(amp2[h], u2[h]);
-                const float ex = UNIFORM ? 1.f : ex2(-sq.x);
-                const float ey = UNIFORM ? 1.f : ex2(-sq.y);
-                float th = sq.x <= umax2 ? w.x * ex : 0.f;
-                if (sq.y <= umax2) th = fmaf(w.y, ey, th);
-                tp[h] = th;
-              }
-#pragma unroll
-              for (int st = 1; st < (G + 1) / 2; st *= 2)
-#pragma unroll
-                for (int h = 0; h + st < (G + 1) / 2; h += 2 * st) tp[h] += tp[h + st];
-              const float t = tp[0];
-              // compensated accumulation: a sample collects the cancelling
-              // pulses of thousands of balls, and a plain FP32 running sum
-              // loses ~1e-5 relative by 1e5 balls.  Dekker's FastTwoSum is
-              // exact when |running sum| >= |t|, which holds after the first
-              // few groups; otherwise its error term loses about eps |t|.
-              float hs, he;
-              fast_two_sum(mytr[k], t, hs, he);
-              mytr[k] = hs;
-              mylo[k] += he;
+            for (int h = 0; h < H; ++h) {
+              const float2 sq = __fmul2_rn(u2[h], u2[h]);
+              const float2 w = __fmul2_rn(amp2[h], u2[h]);
+              const float ex = UNIFORM ? 1.f : ex2(-sq.x);
+              const float ey = UNIFORM ? 1.f : ex2(-sq.y);
+              float th = sq.x <= umax2 ? w.x * ex : 0.f;
+              if (sq.y <= umax2) th = fmaf(w.y, ey, th);
+              tp[h] = th;
             }
 #pragma unroll
-            for (int h = 0; h < (G + 1) / 2; ++h) u2[h] = __fadd2_rn(u2[h], nd2[h]);
+            for (int st = 1; st < H; st *= 2)
+#pragma unroll
+              for (int h = 0; h + st < H; h += 2 * st) tp[h] += tp[h + st];
+            // compensated accumulation: a sample collects the cancelling
+            // pulses of thousands of balls, and a plain FP32 running sum
+            // loses ~1e-5 relative by 1e5 balls.  Dekker's FastTwoSum is
+            // exact when |running sum| >= |t|, which holds after the first
+            // few groups; otherwise its error term loses about eps |t|.
+            float hs, he;
+            fast_two_sum(*pt, tp[0], hs, he);
+            *pt = hs;
+            *pl += he;
+#pragma unroll
+            for (int h = 0; h < H; ++h) u2[h] = __fadd2_rn(u2[h], nd2[h]);
           }
-          __syncwarp();
+          __syncwarp();  // the next group's lanes read what this one wrote
         }
       }
-        }
+    }
     const int abort = __syncthreads_or(!ok);
     if (abort) {
       // A copy did not complete in time: record it and give the copy still in
@@ -369,7 +410,7 @@ __global__ void __launch_bounds__(kMaxThreads, 1) k_forward(const FwdArgs A) {
   const long long b_end = min(A.n, b_begin + A.balls_per_split);
   const float *state_f0 = A.state + (long long)f * 5 * A.stride;
   const int k0 = band_tile_start<UNIFORM>(A.q, state_f0, A.stride, b_begin, b_end, A.s_tile, st, A.t_tile, tt,
-                                          reinterpret_cast<float *>(m.srec));
+                                          m.sgrp);
   if (k0 < 0) return;  // no arrival in this tile; the output was zeroed
   const int klen = min(A.t_tile, T - k0);
   const bool single = A.n_splits == 1;
@@ -406,7 +447,7 @@ __global__ void __launch_bounds__(kMaxThreads, 1) k_forward_batched(const BatchF
     const int f = (int)(local / d.n_stiles);
     const float *state_f0 = d.state + (long long)f * 5 * d.stride;
     const int k0 = band_tile_start<false>(d.q, state_f0, d.stride, 0, d.n, A.s_tile, st, A.t_tile, tt,
-                                          reinterpret_cast<float *>(m.srec));
+                                          m.sgrp);
     if (k0 < 0) continue;  // no arrival in this tile; the traces were zeroed
     const int klen = min(A.t_tile, d.q.T - k0);
     const bool ok = forward_item<false, G>(d.q, d.state + (long long)f * 5 * d.stride, d.stride, 0, d.n, A.s_tile,
@@ -465,8 +506,8 @@ __global__ void k_count(const Acq q, const float *state, long long n, long long 
 }  // namespace
 
 size_t forward_smem_bytes(int s_tile, int t_tile, int nb_tile) {
-  return 128 + sizeof(float) * (size_t)(2 * 5 * nb_tile) + sizeof(float4) * (size_t)(s_tile * 32) +
-         2 * sizeof(float) * (size_t)s_tile * t_tile;
+  return 128 + sizeof(float) * (size_t)(2 * 5 * nb_tile) + sizeof(float) * (size_t)(s_tile * 128) +
+         2 * sizeof(float) * (size_t)s_tile * (t_tile + kRowPad);
 }
 
 namespace {
@@ -493,7 +534,7 @@ int forward_blocks_per_sm(const FwdPlan &p, bool uniform) {
 
 int forward_default_s_tile(int t_tile, int nb_tile) {
   const long long budget = 232448 - 128 - (long long)sizeof(float) * 2 * 5 * nb_tile;
-  const long long per_sensor = 2LL * (long long)sizeof(float) * t_tile + (long long)sizeof(float4) * 32;
+  const long long per_sensor = 2LL * (long long)sizeof(float) * (t_tile + kRowPad) + (long long)sizeof(float) * 128;
   return (int)std::max(1LL, std::min(16LL, budget / per_sensor));
 }
 
