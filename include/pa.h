@@ -197,7 +197,7 @@ PA_API int32_t pa_forward(const pa_geom *geom, const pa_balls *balls, int32_t n_
 
 /* pa_forward with an explicit tile plan, for autotuning.  tiles = {sensors
  * per CTA (1..16, 0 = default), samples per CTA (multiple of 4, 0 = default),
- * balls per TMA stage (multiple of 4, 0 = default), ball splits (0 =
+ * balls per TMA stage (multiple of 4, at most 8192, 0 = default), ball splits (0 =
  * default), pairs swept together per warp (1, 2, 4, 8 or 16; 0 = default)}, a
  * host array of 5, or NULL for the built-in heuristic.  Results equal
  * pa_forward's up to float summation order. */

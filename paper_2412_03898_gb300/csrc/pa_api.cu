@@ -109,13 +109,13 @@ int forward_impl(const pa_geom *geom, const pa_balls *balls, int32_t F, float *t
     return cuda_status(
         cudaMemsetAsync(traces, 0, sizeof(float) * (size_t)F * geom->n_sensors * geom->n_samples, st));
   }
-  if (tiles && (tiles[0] < 0 || tiles[0] > 16 || tiles[1] < 0 || tiles[2] < 0 || tiles[3] < 0 ||
+  if (tiles && (tiles[0] < 0 || tiles[0] > 16 || tiles[1] < 0 || tiles[2] < 0 || tiles[2] > 8192 || tiles[3] < 0 ||
                 (tiles[2] & 3) != 0 || (tiles[1] & 3) != 0 || tiles[4] < 0 || tiles[4] > 16))
     return PA_ERR_INVALID_ARG;
   const pa::FwdPlan p = pa::forward_plan(geom->n_sensors, geom->n_samples, balls->n, F, d->sms,
                                          tiles ? tiles[0] : 0, tiles ? tiles[1] : 0, tiles ? tiles[2] : 0,
                                          tiles ? tiles[3] : 0, tiles ? tiles[4] : 0);
-  if ((int)p.smem > d->max_smem) return PA_ERR_INVALID_ARG;
+  if (p.smem > (size_t)d->max_smem) return PA_ERR_INVALID_ARG;
   if (p.ws_bytes > 0 && (ws == nullptr || ws_bytes < p.ws_bytes || !aligned(ws, 256))) return PA_ERR_WORKSPACE;
   pa::FwdArgs a;
   a.q = make_acq(geom);
@@ -324,7 +324,7 @@ int32_t pa_forward_batched(const pa_scene *scenes, int32_t n_scenes, uint32_t fl
   if (n_scenes < 0 || n_scenes > PA_MAX_SCENES || (n_scenes > 0 && scenes == nullptr)) return PA_ERR_INVALID_ARG;
   if ((flags & ~PA_ACCUMULATE) != 0) return PA_ERR_INVALID_ARG;
   if (tiles && (tiles[0] < 0 || tiles[0] > 16 || tiles[1] < 0 || (tiles[1] & 3) != 0 || tiles[2] < 0 ||
-                (tiles[2] & 3) != 0 || tiles[4] < 0 || tiles[4] > 16))
+                tiles[2] > 8192 || (tiles[2] & 3) != 0 || tiles[4] < 0 || tiles[4] > 16))
     return PA_ERR_INVALID_ARG;
   if (workspace == nullptr || workspace_bytes < pa_batched_workspace_size() || !aligned(workspace, 16))
     return PA_ERR_WORKSPACE;

@@ -37,15 +37,24 @@ namespace {
 constexpr int kMaxThreads = 512;  // at most 16 sensors (warps) per CTA
 constexpr long long kMaxBallsPerSplit = 131072;  // default plans split larger ball sets
 
-constexpr int kRowPad = 32;  // samples of padding after every trace row
+constexpr int kRowPad = 32;   // samples of padding after every trace row
+constexpr int kClasses = 17;  // 16 radius classes + 1 for slots past the tile's end
+
+// Bytes of the per-tile ordering area: class counts [kClasses][nchunk] and
+// the order [nchunk * 32], nchunk = 32-ball chunks per tile.
+__host__ __device__ constexpr int order_bytes(int nb_tile) {
+  return ((((nb_tile + 31) >> 5) * (kClasses * 4 + 32 * 2)) + 15) & ~15;
+}
 
 // Shared-memory layout of a forward CTA.
 struct FwdSmem {
-  uint64_t *bars;  // 2 mbarriers (TMA stages)
-  float *sball;    // [2][5][nb_tile] ball tiles
-  float *sgrp;     // [s_tile][128] group records of the current chunk
-  float *str;      // [s_tile][t_tile + kRowPad] trace tiles (high part)
-  float *strlo;    // [s_tile][t_tile + kRowPad] rounding errors of str (compensated sum)
+  uint64_t *bars;         // 2 mbarriers (TMA stages)
+  float *sball;           // [2][5][nb_tile] ball tiles
+  float *sgrp;            // [s_tile][128] group records of the current chunk
+  int *scnt;              // [kClasses][nchunk] class counts, then their offsets
+  unsigned short *sperm;  // [nchunk * 32] tile positions in sweep order
+  float *str;             // [s_tile][t_tile + kRowPad] trace tiles (high part)
+  float *strlo;           // [s_tile][t_tile + kRowPad] rounding errors of str (compensated sum)
 };
 
 __device__ __forceinline__ FwdSmem fwd_smem(unsigned char *raw, int s_tile, int t_tile, int nb_tile) {
@@ -53,9 +62,63 @@ __device__ __forceinline__ FwdSmem fwd_smem(unsigned char *raw, int s_tile, int 
   m.bars = reinterpret_cast<uint64_t *>(raw);
   m.sball = reinterpret_cast<float *>(raw + 128);
   m.sgrp = m.sball + 2 * 5 * nb_tile;
-  m.str = m.sgrp + s_tile * 128;
+  m.scnt = reinterpret_cast<int *>(m.sgrp + s_tile * 128);
+  m.sperm = reinterpret_cast<unsigned short *>(m.scnt + kClasses * ((nb_tile + 31) >> 5));
+  m.str = reinterpret_cast<float *>(reinterpret_cast<unsigned char *>(m.scnt) + order_bytes(nb_tile));
   m.strlo = m.str + s_tile * (t_tile + kRowPad);
   return m;
+}
+
+// Radius class of a ball: quarter-octaves of a (the float's exponent and two
+// leading mantissa bits), modulo 16.  Balls of one class have windows whose
+// lengths differ by less than 19%.
+__device__ __forceinline__ int radius_class(float a) { return (int)((__float_as_uint(a) >> 21) & 15u); }
+
+// Sweep order of one ball tile: a stable counting sort of the tile's slots by
+// radius class, slots past `cnt` last.  Sorted groups of pairs then have
+// windows of nearly the same length, so the union sweep wastes fewer lanes.
+// The order depends only on the tile's contents (deterministic).  Block-wide:
+// every thread calls it.
+__device__ __forceinline__ void order_tile(const float *ba, int nbt, int cnt, int *scnt, unsigned short *sperm) {
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5, nw = blockDim.x >> 5;
+  const int nchunk = (nbt + 31) >> 5;
+  for (int j = warp; j < nchunk; j += nw) {
+    const int i = j * 32 + lane;
+    const int c = i < cnt ? radius_class(ba[i]) : kClasses - 1;
+#pragma unroll
+    for (int cc = 0; cc < kClasses; ++cc) {
+      const unsigned mk = __ballot_sync(FULL, c == cc);
+      if (lane == cc) scnt[cc * nchunk + j] = __popc(mk);
+    }
+  }
+  __syncthreads();
+  if (warp == 0) {
+    // exclusive scan over (class, chunk), class-major
+    const int E = kClasses * nchunk, L = (E + 31) >> 5;
+    const int e0 = min(lane * L, E), e1 = min(e0 + L, E);
+    int sum = 0;
+    for (int e = e0; e < e1; ++e) sum += scnt[e];
+    int incl = sum;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+      const int v = __shfl_up_sync(FULL, incl, o);
+      if (lane >= o) incl += v;
+    }
+    int run = incl - sum;
+    for (int e = e0; e < e1; ++e) {
+      const int v = scnt[e];
+      scnt[e] = run;
+      run += v;
+    }
+  }
+  __syncthreads();
+  for (int j = warp; j < nchunk; j += nw) {
+    const int i = j * 32 + lane;
+    const int c = i < cnt ? radius_class(ba[i]) : kClasses - 1;
+    const unsigned same = __match_any_sync(FULL, c);
+    sperm[scnt[c * nchunk + j] + __popc(same & ((1u << lane) - 1u))] = (unsigned short)i;
+  }
+  __syncthreads();
 }
 
 // Group records in a warp's 128-float area (16-byte aligned).  G >= 2: per
@@ -132,10 +195,13 @@ __device__ __forceinline__ bool forward_item(const Acq &q, const float *state_f,
     const bool ok = mbar_wait_bounded(&bars[stage], par);
     phase ^= 1u << stage;
     const int cnt = (int)min((long long)nbt, b_end - (b_begin + (long long)t * nbt));
+    const float *bx = sball + stage * 5 * nbt;
+    // (after a timed-out wait the order is built from stale data and unused)
+    order_tile(bx + 3 * nbt, nbt, cnt, m.scnt, m.sperm);
     if (ok && s_ok) {
-      const float *bx = sball + stage * 5 * nbt;
       for (int c0 = 0; c0 < cnt; c0 += 32) {
-        const int bi = c0 + lane;
+        // this lane's ball: position c0 + lane of the tile's sweep order
+        const int bi = c0 + lane < cnt ? (int)m.sperm[c0 + lane] : nbt;
         // cheap FP32 estimate of the window: skip chunks with no pair in this tile
         bool maybe = false;
         if (bi < cnt) {
@@ -507,7 +573,7 @@ __global__ void k_count(const Acq q, const float *state, long long n, long long 
 
 size_t forward_smem_bytes(int s_tile, int t_tile, int nb_tile) {
   return 128 + sizeof(float) * (size_t)(2 * 5 * nb_tile) + sizeof(float) * (size_t)(s_tile * 128) +
-         2 * sizeof(float) * (size_t)s_tile * (t_tile + kRowPad);
+         (size_t)order_bytes(nb_tile) + 2 * sizeof(float) * (size_t)s_tile * (t_tile + kRowPad);
 }
 
 namespace {
@@ -533,7 +599,7 @@ int forward_blocks_per_sm(const FwdPlan &p, bool uniform) {
 }
 
 int forward_default_s_tile(int t_tile, int nb_tile) {
-  const long long budget = 232448 - 128 - (long long)sizeof(float) * 2 * 5 * nb_tile;
+  const long long budget = 232448 - 128 - (long long)sizeof(float) * 2 * 5 * nb_tile - order_bytes(nb_tile);
   const long long per_sensor = 2LL * (long long)sizeof(float) * (t_tile + kRowPad) + (long long)sizeof(float) * 128;
   return (int)std::max(1LL, std::min(16LL, budget / per_sensor));
 }
