@@ -135,15 +135,16 @@ static_assert(32 / 2 * grp_stride<2>() <= 128 && 32 / 4 * grp_stride<4>() <= 128
               "group records exceed a warp's area");
 
 // One work item: frame state `state_f`, sensors [st*s_tile, +s_tile), samples
-// [k0, k0+klen), balls [b_begin, b_end).  Writes (or adds) the trace tile to
+// [k0, k0+klen), balls [b_begin, b_end); `cull` enables a cheap per-chunk
+// window test (for arrival bands wider than one tile).  Writes (or adds) the trace tile to
 // dst_f[s][k] (frame base of a [S][T] array).  `phase` holds the parity of
 // each TMA stage's next completion and is carried across items of a
 // persistent CTA.  Returns false after a bounded wait ran out.
 template <bool UNIFORM, int G>
 __device__ __forceinline__ bool forward_item(const Acq &q, const float *state_f, long long stride,
                                              long long b_begin, long long b_end, int s_tile, int t_tile, int nbt,
-                                             int st, int k0, int klen, float *dst_f, bool acc, const FwdSmem &m,
-                                             unsigned &phase, unsigned *err) {
+                                             int st, int k0, int klen, bool cull, float *dst_f, bool acc,
+                                             const FwdSmem &m, unsigned &phase, unsigned *err) {
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
   const int T = q.T;
   const int s = st * s_tile + warp;
@@ -202,17 +203,21 @@ __device__ __forceinline__ bool forward_item(const Acq &q, const float *state_f,
       for (int c0 = 0; c0 < cnt; c0 += 32) {
         // this lane's ball: position c0 + lane of the tile's sweep order
         const int bi = c0 + lane < cnt ? (int)m.sperm[c0 + lane] : nbt;
-        // cheap FP32 estimate of the window: skip chunks with no pair in this tile
-        bool maybe = false;
-        if (bi < cnt) {
-          const float dx = bx[bi] - sx, dy = bx[nbt + bi] - sy, dz = bx[2 * nbt + bi] - sz;
-          const float a = bx[3 * nbt + bi];
-          const float h = (UNIFORM ? 1.f : q.kappa) * a;
-          const float rc = sqrtf(fmaf(dx, dx, fmaf(dy, dy, dz * dz))) - q.ct0h;
-          const float lo = (rc - h) * q.inv_delta, hi = (rc + h) * q.inv_delta;
-          maybe = a > 0.f && bx[4 * nbt + bi] != 0.f && hi >= (float)(k0 - 2) && lo <= (float)(k0 + klen + 1);
+        if (cull) {
+          // cheap FP32 estimate of the window: skip chunks with no pair in
+          // this tile (only when the arrival band spans several sample
+          // tiles; within one tile it costs more than it saves)
+          bool maybe = false;
+          if (bi < cnt) {
+            const float dx = bx[bi] - sx, dy = bx[nbt + bi] - sy, dz = bx[2 * nbt + bi] - sz;
+            const float a = bx[3 * nbt + bi];
+            const float h = (UNIFORM ? 1.f : q.kappa) * a;
+            const float rc = sqrtf(fmaf(dx, dx, fmaf(dy, dy, dz * dz))) - q.ct0h;
+            const float lo = (rc - h) * q.inv_delta, hi = (rc + h) * q.inv_delta;
+            maybe = a > 0.f && bx[4 * nbt + bi] != 0.f && hi >= (float)(k0 - 2) && lo <= (float)(k0 + klen + 1);
+          }
+          if (__ballot_sync(FULL, maybe) == 0) continue;
         }
-        if (__ballot_sync(FULL, maybe) == 0) continue;
         PairWin w;
         w.W = 0;
         w.u0 = w.du = w.amp = 0.f;
@@ -286,6 +291,8 @@ __device__ __forceinline__ bool forward_item(const Acq &q, const float *state_f,
           }
           float *pt = mytr + kb + lane;
           float *pl = mylo + kb + lane;
+          // two steps per trip: their loads, SFU work and stores interleave
+#pragma unroll 2
           for (int it = 0; it < ns; ++it, pt += 32, pl += 32) {
             // the group's pulses at this sample, summed in registers (one
             // partial sum per ball pair keeps the dependency chains short)
@@ -369,10 +376,12 @@ __device__ __forceinline__ bool forward_item(const Acq &q, const float *state_f,
 // farthest point of the active balls' bounding box, widened by the largest
 // window half-width and two samples.  Returns -1 when the tile holds no
 // arrival (the caller has zeroed the output).  Block-wide: every thread calls
-// it; `red` is shared scratch of at least 8 * (warps + 1) floats.
+// it; `red` is shared scratch of at least 8 * (warps + 1) floats.  `whole`
+// tells whether one tile holds the whole band.
 template <bool UNIFORM>
 __device__ int band_tile_start(const Acq &q, const float *state_f, long long stride, long long b_begin,
-                               long long b_end, int s_tile, int st, int t_tile, int tt, float *red) {
+                               long long b_end, int s_tile, int st, int t_tile, int tt, float *red, bool &whole) {
+  whole = true;
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5, nw = blockDim.x >> 5;
   const float INF = __int_as_float(0x7f800000);
   float v[7] = {INF, INF, INF, -INF, -INF, -INF, 0.f};  // min xyz, max xyz, max a
@@ -446,6 +455,7 @@ __device__ int band_tile_start(const Acq &q, const float *state_f, long long str
   const int kb_hi = (int)fminf(hi, (float)(T - 1));
   const long long start = (long long)kb_lo + (long long)tt * t_tile;
   if (start > kb_hi || start >= T) return -1;
+  whole = kb_lo + (long long)t_tile > kb_hi;
   return (int)start;
 }
 
@@ -475,8 +485,9 @@ __global__ void __launch_bounds__(kMaxThreads, 1) k_forward(const FwdArgs A) {
   const long long b_begin = (long long)split * A.balls_per_split;
   const long long b_end = min(A.n, b_begin + A.balls_per_split);
   const float *state_f0 = A.state + (long long)f * 5 * A.stride;
+  bool whole;
   const int k0 = band_tile_start<UNIFORM>(A.q, state_f0, A.stride, b_begin, b_end, A.s_tile, st, A.t_tile, tt,
-                                          m.sgrp);
+                                          m.sgrp, whole);
   if (k0 < 0) return;  // no arrival in this tile; the output was zeroed
   const int klen = min(A.t_tile, T - k0);
   const bool single = A.n_splits == 1;
@@ -484,7 +495,8 @@ __global__ void __launch_bounds__(kMaxThreads, 1) k_forward(const FwdArgs A) {
                         : A.partial + ((long long)split * A.F + f) * A.q.S * T;
   unsigned phase = 0;
   forward_item<UNIFORM, G>(A.q, A.state + (long long)f * 5 * A.stride, A.stride, b_begin, b_end, A.s_tile, A.t_tile,
-                           A.nb_tile, st, k0, klen, dst_f, single && (A.flags & PA_ACCUMULATE), m, phase, A.err);
+                           A.nb_tile, st, k0, klen, !whole, dst_f, single && (A.flags & PA_ACCUMULATE), m, phase,
+                           A.err);
 }
 
 // Persistent CTAs over the work items of several scenes: an item is
@@ -512,12 +524,14 @@ __global__ void __launch_bounds__(kMaxThreads, 1) k_forward_batched(const BatchF
     const int st = (int)(local % d.n_stiles);
     const int f = (int)(local / d.n_stiles);
     const float *state_f0 = d.state + (long long)f * 5 * d.stride;
+    bool whole;
     const int k0 = band_tile_start<false>(d.q, state_f0, d.stride, 0, d.n, A.s_tile, st, A.t_tile, tt,
-                                          m.sgrp);
+                                          m.sgrp, whole);
     if (k0 < 0) continue;  // no arrival in this tile; the traces were zeroed
     const int klen = min(A.t_tile, d.q.T - k0);
     const bool ok = forward_item<false, G>(d.q, d.state + (long long)f * 5 * d.stride, d.stride, 0, d.n, A.s_tile,
-                                           A.t_tile, A.nb_tile, st, k0, klen, d.out + (long long)f * d.q.S * d.q.T,
+                                           A.t_tile, A.nb_tile, st, k0, klen, !whole,
+                                           d.out + (long long)f * d.q.S * d.q.T,
                                            (A.flags & PA_ACCUMULATE) != 0, m, phase, A.err);
     if (!ok) break;
   }
