@@ -129,7 +129,6 @@ __device__ __forceinline__ void ball_frame_grad(const Acq &q, const float *gfram
           gcur = gnext;
         }
         float s1 = S1.x + S1.y, s3 = S3.x + S3.y, sr = SR.x + SR.y;
-#pragma unroll
         s1 += __shfl_xor_sync(FULL, s1, 1);
         s3 += __shfl_xor_sync(FULL, s3, 1);
         sr += __shfl_xor_sync(FULL, sr, 1);
