@@ -44,6 +44,14 @@ const DevInfo *dev_info() {
 inline bool aligned(const void *p, uintptr_t a) { return (reinterpret_cast<uintptr_t>(p) & (a - 1)) == 0; }
 inline bool finite_pos(float v) { return std::isfinite(v) && v > 0.f; }
 
+// Explicit tile plan {sensors per CTA, samples per CTA, balls per stage,
+// ball splits, pairs per sweep}: NULL, or every entry in range.
+bool tiles_ok(const int32_t *t) {
+  if (t == nullptr) return true;
+  return t[0] >= 0 && t[0] <= 16 && t[1] >= 0 && (t[1] & 3) == 0 && t[2] >= 0 && t[2] <= 8192 &&
+         (t[2] & 3) == 0 && t[3] >= 0 && t[4] >= 0 && t[4] <= 16;
+}
+
 int check_geom(const pa_geom *g) {
   if (g == nullptr || g->sensors == nullptr) return PA_ERR_INVALID_ARG;
   if (g->n_sensors < 1 || g->sensor_stride < g->n_sensors) return PA_ERR_INVALID_ARG;
@@ -109,9 +117,7 @@ int forward_impl(const pa_geom *geom, const pa_balls *balls, int32_t F, float *t
     return cuda_status(
         cudaMemsetAsync(traces, 0, sizeof(float) * (size_t)F * geom->n_sensors * geom->n_samples, st));
   }
-  if (tiles && (tiles[0] < 0 || tiles[0] > 16 || tiles[1] < 0 || tiles[2] < 0 || tiles[2] > 8192 || tiles[3] < 0 ||
-                (tiles[2] & 3) != 0 || (tiles[1] & 3) != 0 || tiles[4] < 0 || tiles[4] > 16))
-    return PA_ERR_INVALID_ARG;
+  if (!tiles_ok(tiles)) return PA_ERR_INVALID_ARG;
   const pa::FwdPlan p = pa::forward_plan(geom->n_sensors, geom->n_samples, balls->n, F, d->sms,
                                          tiles ? tiles[0] : 0, tiles ? tiles[1] : 0, tiles ? tiles[2] : 0,
                                          tiles ? tiles[3] : 0, tiles ? tiles[4] : 0);
@@ -203,7 +209,7 @@ int32_t pa_deform_backward(const pa_canon *canon, const float *t_frames, int32_t
 
 size_t pa_forward_workspace_size_ex(const pa_geom *geom, const pa_balls *balls, int32_t n_frames,
                                     const int32_t *tiles) {
-  if (check_geom(geom) || check_balls(balls) || n_frames <= 0 || balls->n == 0) return 0;
+  if (!tiles_ok(tiles) || check_geom(geom) || check_balls(balls) || n_frames <= 0 || balls->n == 0) return 0;
   const DevInfo *d = dev_info();
   if (!d) return 0;
   const pa::FwdPlan p = pa::forward_plan(geom->n_sensors, geom->n_samples, balls->n, n_frames, d->sms,
@@ -229,7 +235,7 @@ int32_t pa_forward_ex(const pa_geom *geom, const pa_balls *balls, int32_t n_fram
 int32_t pa_forward_plan_info(const pa_geom *geom, const pa_balls *balls, int32_t n_frames, const int32_t *tiles,
                              int32_t *out7) {
   if (out7 == nullptr) return PA_ERR_INVALID_ARG;
-  if (tiles && (tiles[0] < 0 || tiles[0] > 16 || tiles[4] < 0 || tiles[4] > 16)) return PA_ERR_INVALID_ARG;
+  if (!tiles_ok(tiles)) return PA_ERR_INVALID_ARG;
   int rc = check_geom(geom);
   if (rc) return rc;
   if ((rc = check_balls(balls))) return rc;
@@ -323,9 +329,7 @@ int32_t pa_forward_batched(const pa_scene *scenes, int32_t n_scenes, uint32_t fl
                            void *workspace, size_t workspace_bytes, void *stream) {
   if (n_scenes < 0 || n_scenes > PA_MAX_SCENES || (n_scenes > 0 && scenes == nullptr)) return PA_ERR_INVALID_ARG;
   if ((flags & ~PA_ACCUMULATE) != 0) return PA_ERR_INVALID_ARG;
-  if (tiles && (tiles[0] < 0 || tiles[0] > 16 || tiles[1] < 0 || (tiles[1] & 3) != 0 || tiles[2] < 0 ||
-                tiles[2] > 8192 || (tiles[2] & 3) != 0 || tiles[4] < 0 || tiles[4] > 16))
-    return PA_ERR_INVALID_ARG;
+  if (!tiles_ok(tiles)) return PA_ERR_INVALID_ARG;
   if (workspace == nullptr || workspace_bytes < pa_batched_workspace_size() || !aligned(workspace, 16))
     return PA_ERR_WORKSPACE;
   const DevInfo *d = dev_info();

@@ -607,8 +607,13 @@ FwdKernel forward_kernel(bool uniform, int group) {
 int forward_blocks_per_sm(const FwdPlan &p, bool uniform) {
   int nb = 0;
   auto fn = forward_kernel(uniform, p.group);
-  cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)p.smem);
-  cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, fn, 32 * p.s_tile, p.smem);
+  if (cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)p.smem) != cudaSuccess ||
+      cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, fn, 32 * p.s_tile, p.smem) != cudaSuccess) {
+    // a plan larger than shared memory: the caller rejects it; leave no
+    // pending error for the next launch's cudaGetLastError
+    (void)cudaGetLastError();
+    return 0;
+  }
   return nb;
 }
 

@@ -102,3 +102,17 @@ def test_imaging_and_chain_rule_args_rejected_on_host(lib):
     null_gr = _lib.pa_grads(16, None, 16, 16)
     assert lib.pa_deform_backward(ctypes.byref(canon), fake, 2, fake, ctypes.byref(null_gr), 0, None) == E
     assert lib.pa_deform_backward(ctypes.byref(canon), fake, 2, fake, ctypes.byref(gr), 1 << 5, None) == E
+
+
+def test_invalid_tile_plans_rejected_on_host(lib):
+    from paper_2412_03898_gb300 import _lib
+    g = _lib.pa_geom(16, 4, 4, 1.5, 40.0, 0.0, 64, 5.0)  # pointers never dereferenced
+    b = _lib.pa_balls(16, 10, 12)
+    out7 = (ctypes.c_int32 * 7)()
+    for bad in ((17, 0, 0, 0, 0), (16, 6, 0, 0, 0), (16, 0, 8196, 0, 0), (16, 0, 6, 0, 0), (16, 0, 0, -1, 0),
+                (16, 0, 0, 0, 17), (-1, 0, 0, 0, 0)):
+        t = (ctypes.c_int32 * 5)(*bad)
+        assert lib.pa_forward_plan_info(ctypes.byref(g), ctypes.byref(b), 1, t, out7) == _lib.PA_ERR_INVALID_ARG, bad
+        assert lib.pa_forward_workspace_size_ex(ctypes.byref(g), ctypes.byref(b), 1, t) == 0, bad
+        assert lib.pa_forward_ex(ctypes.byref(g), ctypes.byref(b), 1, None, 0, t, None, 0, None) == \
+            _lib.PA_ERR_INVALID_ARG, bad

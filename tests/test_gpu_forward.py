@@ -129,6 +129,10 @@ def test_invalid_arguments_are_rejected(pa):
     st = dev_pad(sc.balls)[None]
     with pytest.raises(pa.PAError):
         pa.forward(geom, st, 10, tiles=(17, 0, 0, 0))
+    with pytest.raises(pa.PAError):  # more balls per stage than any shared memory holds
+        pa.forward(geom, st, 10, tiles=(16, 0, 8196, 0, 8))
+    with pytest.raises(pa.PAError):  # the batched entry point checks the same bound
+        pa.forward_batched([pa.Scene(geom, st, 10)], tiles=(16, 0, 8196, 0, 8))
     bad = pa.Geometry(geom.sensors, sc.c, sc.fs, sc.t0, 62, sc.kappa)  # T % 4 != 0
     with pytest.raises(pa.PAError):
         pa.forward(bad, st, 10)
