@@ -60,7 +60,10 @@ __device__ __forceinline__ void fast_two_sum(float a, float b, float &s, float &
 // |b - s| as a double-float (hi, lo), relative error ~2^-44, from fp32
 // coordinates.  The coordinate differences are exact (TwoSum), the squares
 // exact to first order (TwoProd), the sum compensated, and the square root
-// refined by one Newton step on the residual.
+// refined by one Newton step on the residual.  The step starts from
+// x * rsqrt(x) (a few ulp): its error after the step is of order ulp^2, so a
+// correctly rounded square root would buy nothing.  (hi, lo) is not
+// normalised (|lo| can reach a few ulp of hi); callers renormalise.
 __device__ __forceinline__ void distance_df(float bx, float by, float bz, float sx, float sy,
                                             float sz, float &rh, float &rl) {
   float dxh, dxl, dyh, dyl, dzh, dzl;
@@ -77,9 +80,10 @@ __device__ __forceinline__ void distance_df(float bx, float by, float bz, float 
   float lo = __fadd_rn(__fadd_rn(e1, e2), __fadd_rn(__fadd_rn(pxl, pyl), pzl));
   float sh, sl;
   fast_two_sum(s2, lo, sh, sl);
-  float r = __fsqrt_rn(sh);
+  const float y = rsqrtf(sh);
+  const float r = __fmul_rn(sh, y);
   rh = r;
-  rl = __fmul_rn(__fadd_rn(fmaf(-r, r, sh), sl), __fdividef(0.5f, r));
+  rl = __fmul_rn(__fadd_rn(fmaf(-r, r, sh), sl), 0.5f * y);
 }
 
 // ---------------------------------------------------------------------------
