@@ -294,30 +294,27 @@ __device__ __forceinline__ bool forward_item(const Acq &q, const float *state_f,
           // two steps per trip: their loads, SFU work and stores interleave
 #pragma unroll 2
           for (int it = 0; it < ns; ++it, pt += 32, pl += 32) {
-            // the group's pulses at this sample, summed in registers (one
-            // partial sum per ball pair keeps the dependency chains short)
-            float tp[H];
+            // the group's pulses at this sample, summed in one register: a
+            // predicated FMA per ball inside its window (fewer instructions
+            // than a select per ball and a tree of partial sums; the two
+            // unrolled steps give the independent chains)
+            float t = 0.f;
 #pragma unroll
             for (int h = 0; h < H; ++h) {
               const float2 sq = __fmul2_rn(u2[h], u2[h]);
               const float2 w = __fmul2_rn(amp2[h], u2[h]);
               const float ex = UNIFORM ? 1.f : ex2(-sq.x);
               const float ey = UNIFORM ? 1.f : ex2(-sq.y);
-              float th = sq.x <= umax2 ? w.x * ex : 0.f;
-              if (sq.y <= umax2) th = fmaf(w.y, ey, th);
-              tp[h] = th;
+              if (sq.x <= umax2) t = fmaf(w.x, ex, t);
+              if (sq.y <= umax2) t = fmaf(w.y, ey, t);
             }
-#pragma unroll
-            for (int st = 1; st < H; st *= 2)
-#pragma unroll
-              for (int h = 0; h + st < H; h += 2 * st) tp[h] += tp[h + st];
             // compensated accumulation: a sample collects the cancelling
             // pulses of thousands of balls, and a plain FP32 running sum
             // loses ~1e-5 relative by 1e5 balls.  Dekker's FastTwoSum is
             // exact when |running sum| >= |t|, which holds after the first
             // few groups; otherwise its error term loses about eps |t|.
             float hs, he;
-            fast_two_sum(*pt, tp[0], hs, he);
+            fast_two_sum(*pt, t, hs, he);
             *pt = hs;
             *pl += he;
 #pragma unroll
