@@ -349,7 +349,7 @@ int32_t pa_forward_batched(const pa_scene *scenes, int32_t n_scenes, uint32_t fl
   t_tile = std::min(std::min(t_tile, maxT), 16384);
   const int nb_tile = tiles && tiles[2] > 0 ? tiles[2] : 512;
   const int s_tile = tiles && tiles[0] > 0 ? tiles[0] : pa::forward_default_s_tile(t_tile, nb_tile);
-  const int group = tiles && (tiles[4] == 1 || tiles[4] == 2 || tiles[4] == 4 || tiles[4] == 16) ? tiles[4] : 8;
+  const int group = tiles && (tiles[4] == 1 || tiles[4] == 2 || tiles[4] == 4 || tiles[4] == 8) ? tiles[4] : 16;
   const size_t smem = pa::forward_smem_bytes(s_tile, t_tile, nb_tile);
   if ((long long)smem > d->max_smem) return PA_ERR_INVALID_ARG;
   // scenes with balls, heaviest items (most balls) first
