@@ -58,11 +58,18 @@ KERNEL_SOURCES = {
 
 
 def sources_sha256(kind: str) -> str:
+    """SHA-256 of the kernel's sources with comments and blank lines removed,
+    so that edits to comments alone keep a recorded capture valid."""
     import hashlib
+    import re
     h = hashlib.sha256()
     for name in KERNEL_SOURCES[kind]:
-        with open(os.path.join(ROOT, "paper_2412_03898_gb300", "csrc", name), "rb") as fh:
-            h.update(fh.read())
+        with open(os.path.join(ROOT, "paper_2412_03898_gb300", "csrc", name)) as fh:
+            src = fh.read()
+        src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
+        src = re.sub(r"//[^\n]*", "", src)
+        code = "\n".join(line.rstrip() for line in src.splitlines() if line.strip())
+        h.update(code.encode())
     return h.hexdigest()
 
 

@@ -9,6 +9,8 @@
 //  - Ball tiles (x, y, z, a, p rows of nb_tile balls) are streamed from HBM
 //    into shared memory by TMA bulk copies (cp.async.bulk) completing on
 //    mbarriers, double buffered, issued by one thread.
+//  - Each landed ball tile is swept in radius-class order (a stable in-CTA
+//    counting sort), so that grouped windows have similar lengths.
 //  - Per 32-ball chunk, the 32 lanes compute the window and phase of 32
 //    (ball, sensor) pairs in parallel (double-float distance, once per pair).
 //    The warp sorts the pairs by first sample (bitonic network on shuffles);
@@ -16,11 +18,12 @@
 //    pairs gets one shared-memory record with its first sample, its step
 //    count and every member's phase at that sample.  The warp sweeps each
 //    group over the union of its windows: each lane owns one sample of a
-//    32-sample step, adds the G balls' pulses to it in a register
+//    32-sample step and adds the G balls' pulses to it in one register, one
+//    predicated FMA per ball,
 //        u -= 32 du;  v = amp u 2^(-u^2)  if |u| <= kappa K_S
-//    and does one shared-memory load and store per sample and group.  Sorted
-//    groups overlap almost completely, so the sweep wastes few lanes while
-//    giving G independent dependency chains per step.  Trace rows carry 32
+//    then does one compensated shared-memory update per sample and group.
+//    Sorted groups overlap almost completely, so the sweep wastes few lanes;
+//    two steps per loop trip give independent chains.  Trace rows carry 32
 //    samples of padding, so a group's last step needs no bound test (lanes
 //    past every window add an exact zero).
 //  - Trace tiles are flushed with coalesced float4 stores.  With more than
