@@ -139,9 +139,9 @@ static_assert(32 / 2 * grp_stride<2>() <= 128 && 32 / 4 * grp_stride<4>() <= 128
 
 // One work item: frame state `state_f`, sensors [st*s_tile, +s_tile), samples
 // [k0, k0+klen), balls [b_begin, b_end); `cull` enables a cheap per-chunk
-// window test (for arrival bands wider than one tile).  Writes (or adds) the trace tile to
-// dst_f[s][k] (frame base of a [S][T] array).  `phase` holds the parity of
-// each TMA stage's next completion and is carried across items of a
+// window test (for arrival bands wider than one tile).  Writes (or adds) the
+// trace tile to dst_f[s][k] (frame base of a [S][T] array).  `phase` holds the
+// parity of each TMA stage's next completion and is carried across items of a
 // persistent CTA.  Returns false after a bounded wait ran out.
 template <bool UNIFORM, int G>
 __device__ __forceinline__ bool forward_item(const Acq &q, const float *state_f, long long stride,
