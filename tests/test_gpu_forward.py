@@ -52,6 +52,37 @@ def test_forward_long_windows(pa, group):
     assert rel_l2(y.cpu().numpy(), y_o) <= TRACE_TOL
 
 
+def _wide_radius_scene():
+    # radii log-uniform over 0.03-1.5 mm: about 23 quarter-octave radius
+    # classes, so the per-tile class order wraps modulo 16, and windows from
+    # 8 to 400 samples; the widest are clipped at sample 0
+    sc = pa_inputs.small_scene(seed=11, n_balls=3001, n_sensors=19, n_samples=1024)
+    rng = np.random.default_rng(11)
+    sc.balls[3] = np.exp(rng.uniform(np.log(0.03), np.log(1.5), sc.n_balls)).astype(np.float32)
+    return sc
+
+
+@pytest.mark.parametrize("tiles", [None, (8, 512, 100, 2, 16), (16, 1024, 512, 0, 8), (3, 256, 36, 5, 4)])
+def test_forward_parity_wide_radius_range(pa, tiles):
+    sc = _wide_radius_scene()
+    y = pa.forward(geometry(sc), dev_pad(sc.balls)[None], sc.n_balls, tiles=tiles)
+    pa.device_error()
+    y_o, _ = _oracle_traces(sc)
+    assert rel_l2(y.cpu().numpy(), y_o) <= TRACE_TOL
+
+
+def test_adjoint_parity_wide_radius_range(pa):
+    from gpu_common import GRAD_TOL
+    sc = _wide_radius_scene()
+    g = np.random.default_rng(12).standard_normal((1, sc.n_sensors, sc.n_samples)).astype(np.float32)
+    got = pa.adjoint(geometry(sc), torch.from_numpy(g).cuda(), state=dev_pad(sc.balls)[None], n=sc.n_balls)
+    pa.device_error()
+    want = oracle.adjoint_state(sc.balls[None], sc.sensors, sc.c, sc.fs, sc.t0, sc.n_samples, sc.kappa, g)
+    got = got[..., :sc.n_balls].cpu().numpy()
+    for ch in range(5):
+        assert rel_l2(got[:, ch], want[:, ch]) <= GRAD_TOL, ch
+
+
 def test_forward_multiframe_and_accumulate(pa):
     sc = pa_inputs.small_scene(seed=2, n_balls=517, n_sensors=9, n_samples=512, n_frames=4)
     geom = geometry(sc)
