@@ -41,11 +41,14 @@ constexpr int kAdjWarps = 8;
 // samples.  Returns the totals (identical in every lane).
 // Sensor coordinates are read from sens[c * sstr + s] (shared memory, or the
 // global sensor array of a batched scene).
+template <bool ALLOW_WIDE>
 __device__ __forceinline__ void ball_frame_grad(const Acq &q, const float *gframe, const float *sens, int sstr,
                                                 float4 *rec, int lane, float bx, float by, float bz, float a,
                                                 float p, float out[5], bool &dom) {
   const int S = q.S, T = q.T;
   const float mbias = window_bias((q.kappa * K_S) * (q.kappa * K_S));
+  // 256-bit residual loads need 32-byte aligned rows
+  const bool wide = ALLOW_WIDE && (T & 7) == 0 && (reinterpret_cast<uintptr_t>(gframe) & 31) == 0;
   float gx = 0.f, gy = 0.f, gz = 0.f, ga = 0.f, gp = 0.f;
   if (a > 0.f && p != 0.f) {
     for (int s0 = 0; s0 < S; s0 += 32) {
@@ -98,7 +101,7 @@ __device__ __forceinline__ void ball_frame_grad(const Acq &q, const float *gfram
         const int ka = klo & ~3;
         const float4 *row = reinterpret_cast<const float4 *>(gframe + (long long)__float_as_int(a2.w) * T);
         const int nit = act ? ((khi - ka) >> 3) + 1 : 0;
-        const int nmax = __reduce_max_sync(FULL, nit);
+        const int nmax = wide ? 0 : __reduce_max_sync(FULL, nit);
         int kk = ka + 4 * sl;
         const float du = a0.y;
         float2 ua, ub;  // u at kk, kk + 1 and kk + 2, kk + 3
@@ -119,14 +122,52 @@ __device__ __forceinline__ void ball_frame_grad(const Acq &q, const float *gfram
           SR = __ffma2_rn(ge, __ffma2_rn(sq, negk, one), SR);                        // sum g E (1 - tau^2/a^2)
         };
         const float4 zero4 = make_float4(0.f, 0.f, 0.f, 0.f);
-        float4 gcur = kk <= khi ? __ldg(row + (kk >> 2)) : zero4;
-        for (int it = 0; it < nmax; ++it, kk += 8) {
-          const float4 gnext = kk + 8 <= khi ? __ldg(row + ((kk + 8) >> 2)) : zero4;
-          half(ua, make_float2(gcur.x, gcur.y));
-          half(ub, make_float2(gcur.z, gcur.w));
-          ua = __fadd2_rn(ua, nd2);
-          ub = __fadd2_rn(ub, nd2);
-          gcur = gnext;
+        if (wide) {
+          // 256-bit loads: each lane eight consecutive samples per 16-sample
+          // step, from a 32-byte aligned start (rows are 32-byte aligned when
+          // T % 8 == 0; a load starting at k <= khi <= T - 1 with k % 8 == 0
+          // ends at k + 7 <= T - 1)
+          const int ka8 = klo & ~7;
+          const float *rowf = gframe + (long long)__float_as_int(a2.w) * T;
+          const int nit8 = act ? ((khi - ka8) >> 4) + 1 : 0;
+          const int nmax8 = __reduce_max_sync(FULL, nit8);
+          int k8 = ka8 + 8 * sl;
+          float2 uc, ud;  // u at k8 + 4, k8 + 5 and k8 + 6, k8 + 7
+          ua.x = fmaf((float)(k8 - klo), -du, a0.x);
+          ua.y = ua.x - du;
+          ub.x = fmaf(-2.f, du, ua.x);
+          ub.y = fmaf(-3.f, du, ua.x);
+          uc.x = fmaf(-4.f, du, ua.x);
+          uc.y = fmaf(-5.f, du, ua.x);
+          ud.x = fmaf(-6.f, du, ua.x);
+          ud.y = fmaf(-7.f, du, ua.x);
+          const float2 nd16 = make_float2(-16.f * du, -16.f * du);
+          float4 c0 = zero4, c1 = zero4;
+          if (k8 <= khi) ldg8(rowf + k8, c0, c1);
+          for (int it = 0; it < nmax8; ++it, k8 += 16) {
+            float4 n0 = zero4, n1 = zero4;
+            if (k8 + 16 <= khi) ldg8(rowf + k8 + 16, n0, n1);
+            half(ua, make_float2(c0.x, c0.y));
+            half(ub, make_float2(c0.z, c0.w));
+            half(uc, make_float2(c1.x, c1.y));
+            half(ud, make_float2(c1.z, c1.w));
+            ua = __fadd2_rn(ua, nd16);
+            ub = __fadd2_rn(ub, nd16);
+            uc = __fadd2_rn(uc, nd16);
+            ud = __fadd2_rn(ud, nd16);
+            c0 = n0;
+            c1 = n1;
+          }
+        } else {
+          float4 gcur = kk <= khi ? __ldg(row + (kk >> 2)) : zero4;
+          for (int it = 0; it < nmax; ++it, kk += 8) {
+            const float4 gnext = kk + 8 <= khi ? __ldg(row + ((kk + 8) >> 2)) : zero4;
+            half(ua, make_float2(gcur.x, gcur.y));
+            half(ub, make_float2(gcur.z, gcur.w));
+            ua = __fadd2_rn(ua, nd2);
+            ub = __fadd2_rn(ub, nd2);
+            gcur = gnext;
+          }
         }
         float s1 = S1.x + S1.y, s3 = S3.x + S3.y, sr = SR.x + SR.y;
         s1 += __shfl_xor_sync(FULL, s1, 1);
@@ -181,7 +222,7 @@ __global__ void __launch_bounds__(32 * kAdjWarps) k_adjoint_static(const AdjArgs
 #pragma unroll
     for (int c = 0; c < 5; ++c) v[c] = __shfl_sync(FULL, mine, c);
     float g[5];
-    ball_frame_grad(A.q, A.g + (long long)f * A.q.S * A.q.T, ssens, A.q.S, rec, lane, v[0], v[1], v[2], v[3],
+    ball_frame_grad<true>(A.q, A.g + (long long)f * A.q.S * A.q.T, ssens, A.q.S, rec, lane, v[0], v[1], v[2], v[3],
                        v[4], g, dom);
     const float sc = A.frame_scale ? __ldg(A.frame_scale + f) : 1.f;
     if (lane < 5) {
@@ -253,7 +294,7 @@ __global__ void __launch_bounds__(32 * kAdjWarps, 4) k_adjoint_4d(const AdjArgs 
           H[c] = warp_sum(h);
         }
         float g[5];
-        ball_frame_grad(A.q, A.g + (long long)f * A.q.S * A.q.T, ssens, A.q.S, rec, lane, q0[0] * (1.f + H[0]),
+        ball_frame_grad<false>(A.q, A.g + (long long)f * A.q.S * A.q.T, ssens, A.q.S, rec, lane, q0[0] * (1.f + H[0]),
                         q0[1] * (1.f + H[1]), q0[2] * (1.f + H[2]), q0[3] * (1.f + H[3]), q0[4] * (1.f + H[4]), g,
                         dom);
         const float sc = A.frame_scale ? __ldg(A.frame_scale + f) : 1.f;
@@ -336,7 +377,7 @@ __global__ void __launch_bounds__(32 * kAdjWarps) k_adjoint_batched(const BatchA
 #pragma unroll
       for (int c = 0; c < 5; ++c) v[c] = __shfl_sync(FULL, mine, c);
       float g[5];
-      ball_frame_grad(d.q, d.g + (long long)f * d.q.S * d.q.T, d.q.sensors, d.q.sstride, rec, lane, v[0], v[1], v[2],
+      ball_frame_grad<true>(d.q, d.g + (long long)f * d.q.S * d.q.T, d.q.sensors, d.q.sstride, rec, lane, v[0], v[1], v[2],
                       v[3], v[4], g, dom);
       if (lane < 5) {
         float gv = g[0];

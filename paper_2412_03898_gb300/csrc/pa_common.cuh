@@ -95,6 +95,14 @@ __device__ __forceinline__ float ex2(float x) {
   return y;
 }
 
+// Eight consecutive floats from read-only global memory in one 256-bit load
+// (PTX ld.global.nc.v8.f32, sm_100 and later); p must be 32-byte aligned.
+__device__ __forceinline__ void ldg8(const float *p, float4 &lo, float4 &hi) {
+  asm volatile("ld.global.nc.v8.f32 {%0, %1, %2, %3, %4, %5, %6, %7}, [%8];"
+               : "=f"(lo.x), "=f"(lo.y), "=f"(lo.z), "=f"(lo.w), "=f"(hi.x), "=f"(hi.y), "=f"(hi.z), "=f"(hi.w)
+               : "l"(p));
+}
+
 __device__ __forceinline__ unsigned long long global_ns() {
   unsigned long long t;
   asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
