@@ -28,6 +28,7 @@
 //   dv/dR = -A tau E/R + A E (1 - tau^2/a^2) -> dR = S1 * (-A a/(R K_S)) + A SR
 //   dR/dmu = (mu - x_s)/R.
 #include <algorithm>
+#include <type_traits>
 
 #include "pa_internal.h"
 
@@ -144,20 +145,50 @@ __device__ __forceinline__ void ball_frame_grad(const Acq &q, const float *gfram
           const float2 nd16 = make_float2(-16.f * du, -16.f * du);
           float4 c0 = zero4, c1 = zero4;
           if (k8 <= khi) ldg8(rowf + k8, c0, c1);
-          for (int it = 0; it < nmax8; ++it, k8 += 16) {
+          auto halfu = [&](const float2 u2, const float2 g2) {  // `half` without the window mask
+            const float2 sq = __fmul2_rn(u2, u2);
+            const float2 E = make_float2(ex2(-sq.x), ex2(-sq.y));
+            const float2 ge = __fmul2_rn(g2, E);
+            const float2 gu = __fmul2_rn(ge, u2);
+            S1 = __fadd2_rn(S1, gu);
+            S3 = __ffma2_rn(gu, sq, S3);
+            SR = __ffma2_rn(ge, __ffma2_rn(sq, negk, one), SR);
+          };
+          auto step = [&](auto masked) {
             float4 n0 = zero4, n1 = zero4;
             if (k8 + 16 <= khi) ldg8(rowf + k8 + 16, n0, n1);
-            half(ua, make_float2(c0.x, c0.y));
-            half(ub, make_float2(c0.z, c0.w));
-            half(uc, make_float2(c1.x, c1.y));
-            half(ud, make_float2(c1.z, c1.w));
+            if (decltype(masked)::value) {
+              half(ua, make_float2(c0.x, c0.y));
+              half(ub, make_float2(c0.z, c0.w));
+              half(uc, make_float2(c1.x, c1.y));
+              half(ud, make_float2(c1.z, c1.w));
+            } else {
+              halfu(ua, make_float2(c0.x, c0.y));
+              halfu(ub, make_float2(c0.z, c0.w));
+              halfu(uc, make_float2(c1.x, c1.y));
+              halfu(ud, make_float2(c1.z, c1.w));
+            }
             ua = __fadd2_rn(ua, nd16);
             ub = __fadd2_rn(ub, nd16);
             uc = __fadd2_rn(uc, nd16);
             ud = __fadd2_rn(ud, nd16);
             c0 = n0;
             c1 = n1;
+            k8 += 16;
+          };
+          // Only a walk's first and last step can hold samples outside its
+          // window: steps 1 .. nit8 - 2 lie strictly inside it (the mask is
+          // exactly 1 there).  Steps inside every active sub-warp's walk skip
+          // the mask; the split is warp-uniform.
+          const int mn = __reduce_min_sync(FULL, act ? nit8 : 0x7fffffff);
+          int it = 0;
+          if (nmax8 > 0) {
+            step(std::true_type{});
+            ++it;
           }
+          const int e1 = min(mn - 1, nmax8);
+          for (; it < e1; ++it) step(std::false_type{});
+          for (; it < nmax8; ++it) step(std::true_type{});
         } else {
           float4 gcur = kk <= khi ? __ldg(row + (kk >> 2)) : zero4;
           for (int it = 0; it < nmax; ++it, kk += 8) {
@@ -202,7 +233,7 @@ __device__ __forceinline__ void load_sensors(const AdjArgs &A, float *ssens) {
 }
 
 // Static mode: item = (frame, ball).
-__global__ void __launch_bounds__(32 * kAdjWarps) k_adjoint_static(const AdjArgs A) {
+__global__ void __launch_bounds__(32 * kAdjWarps, 4) k_adjoint_static(const AdjArgs A) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   float4 *recs = reinterpret_cast<float4 *>(smem_raw);
   float *ssens = reinterpret_cast<float *>(recs + kAdjWarps * 96);
