@@ -177,3 +177,27 @@ def test_adjoint_full_size_sampled_balls(pa):
     got = got[0][:, pick].cpu().numpy()
     for ch in range(5):
         assert rel_l2(got[ch], want[0, ch]) <= GRAD_TOL
+
+
+def test_adjoint_wide_and_float4_walks_agree(pa):
+    # A 32-byte aligned residual with T % 8 == 0 takes the 256-bit walk; the
+    # same values at a 16-byte (not 32-byte) aligned address take the float4
+    # walk.  Both must match the oracle and each other (summation order only).
+    sc = pa_inputs.small_scene(seed=71, n_balls=701, n_sensors=23, n_samples=1024)
+    geom = geometry(sc)
+    st = dev_pad(sc.balls)[None]
+    g = np.random.default_rng(71).standard_normal((1, sc.n_sensors, sc.n_samples)).astype(np.float32)
+    g32 = torch.from_numpy(g).cuda()
+    assert g32.data_ptr() % 32 == 0
+    buf = torch.empty(g.size + 4, device="cuda")
+    g16 = buf[4:].view(1, sc.n_sensors, sc.n_samples)
+    g16.copy_(g32)
+    assert g16.data_ptr() % 16 == 0 and g16.data_ptr() % 32 != 0
+    wide = pa.adjoint(geom, g32, state=st, n=sc.n_balls)[..., :sc.n_balls].cpu().numpy()
+    narrow = pa.adjoint(geom, g16, state=st, n=sc.n_balls)[..., :sc.n_balls].cpu().numpy()
+    pa.device_error()
+    want = oracle.adjoint_state(sc.balls[None], sc.sensors, sc.c, sc.fs, sc.t0, sc.n_samples, sc.kappa, g)
+    for ch in range(5):
+        assert rel_l2(wide[:, ch], want[:, ch]) <= GRAD_TOL, ch
+        assert rel_l2(narrow[:, ch], want[:, ch]) <= GRAD_TOL, ch
+        assert rel_l2(wide[:, ch], narrow[:, ch]) <= 1e-5, ch
