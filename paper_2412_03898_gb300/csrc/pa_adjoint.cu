@@ -8,8 +8,9 @@
 //    over all sensors.  The 32 lanes compute the window, phase and gradient
 //    factors of 32 (ball, sensor) pairs in parallel and publish them,
 //    compacted, in shared memory; the warp then walks sixteen pairs at a
-//    time, one per 2-lane sub-warp, each lane on four consecutive samples
-//    per step (a float4 residual load from L2, packed FP32x2 arithmetic,
+//    time, one per 2-lane sub-warp, each lane on eight consecutive samples
+//    per step (one 256-bit residual load from L2 when the rows are 32-byte
+//    aligned, else four samples per float4 load; packed FP32x2 arithmetic;
 //    next step's load in flight), accumulating per lane
 //        S1 = sum g E u,  S3 = sum g E u^3,  SR = sum g E (1 - tau^2/a^2)
 //    which one shuffle between the sub-warp's two lanes turns into the
@@ -81,13 +82,13 @@ __device__ __forceinline__ void ball_frame_grad(const Acq &q, const float *gfram
       }
       __syncwarp();
       // Sixteen pairs at a time, one per 2-lane sub-warp: each sub-warp walks
-      // its pair's whole window, each lane four consecutive samples per step
-      // (one float4 residual load, two packed FP32x2 halves), the next step's
-      // load issued before the current step's arithmetic.  All pairs belong
-      // to one ball, so their windows have nearly the same length and the
-      // sub-warps finish together.  Samples of the aligned float4s outside
-      // the window get weight 0 from the window mask (u^2 <= (kappa K_S)^2,
-      // the forward's own test).
+      // its pair's whole window, each lane eight (or four) consecutive
+      // samples per step (one 256-bit or float4 residual load, packed FP32x2
+      // halves), the next step's load issued before the current step's
+      // arithmetic.  All pairs belong to one ball, so their windows have
+      // nearly the same length and the sub-warps finish together.  Samples
+      // of the aligned loads outside the window get weight 0 from the window
+      // mask (u^2 <= (kappa K_S)^2, the forward's own test).
       const int sub = lane >> 1, sl = lane & 1;
       const float2 negk = make_float2(-K_2LN2, -K_2LN2), one = make_float2(1.f, 1.f);
       for (int g0 = 0; g0 < nv; g0 += 16) {
