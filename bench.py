@@ -9,8 +9,8 @@ dominant kernel's roofline, the FP64 oracle timed on the host cores, 4D IR
 iterations/s (100k balls x 20 frames) batched in a CUDA graph vs plain
 per-frame launches, 16 uneven scenes in persistent launches, the imaging
 tools (UBP, splat, MAP, SSIM) on the simulated heart, and the 4D
-reconstruction quality against ground truth next to UBP; --large4d adds one
-IR iteration on 1M balls x 50 frames.
+reconstruction quality against ground truth next to UBP, and the 4D IR
+iteration on 1M balls x 50 frames, batched in a CUDA graph vs per-frame.
 
   python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
 
@@ -36,15 +36,15 @@ sys.path.insert(0, ROOT)
 
 METRIC = "ball-sensor-sample contributions/sec (fwd+adjoint) and 4D IR iterations/sec vs per-frame"
 UNIT = "contributions/s"
-# Algorithmic FP32 operations per contribution (an FMA counts as one
-# operation): forward u-step, u^2, amp*u, FMA-accumulate = 4 (+1 ex2 on the
-# SFU); adjoint u-step, u^2, G*E, *u, S1 add, S3 FMA, (1-tau^2/a^2) FMA, SR FMA
-# = 8 (+1 ex2).  Peak FP32 operations/s = 152 SMs x 128 lanes x max SM clock.
-FWD_OPS = 4
-ADJ_OPS = 8
-SMS = 152
-FP32_LANES = 128
+# Algorithmic FP32 operations per contribution (one in-window (frame, sensor,
+# ball, sample) term), an FMA counting as one operation: forward 6 (tau step,
+# tau^2, scale, A*tau, *E, accumulate) and adjoint 10, each plus one ex2 on the
+# SFU.  These are the per-contribution counts the roofline is reported on.
+FWD_OPS = 6
+ADJ_OPS = 10
+EX2_PER_CONTRIB = 1
 SM_MAX_MHZ_NOMINAL = 2070.0
+FP32_LANES_NOMINAL = 128
 
 # DRAM traffic per launch (ncu dram__bytes_read.sum + dram__bytes_write.sum)
 # of the static-100k step's kernels, recorded with the SHA-256 of the sources
@@ -86,6 +86,16 @@ def recorded_traffic(kind: str):
     return rec.get("bytes_per_step")
 
 
+def fp32_peak(rates: dict, sms: int) -> dict:
+    """FP32 and ex2 peaks of this GPU from its measured unit rates: the faster
+    of the scalar and packed FMA lane rates, and the SFU ex2 rate, per SM per
+    clock, times the SM count and the clock seen during the probe."""
+    lanes = max(rates["ffma_lanes_per_sm_clk"], rates["ffma2_lanes_per_sm_clk"])
+    mhz = rates["sm_mhz"]
+    return {"lanes_per_sm_clk": lanes, "sm_mhz": mhz, "ops_per_s": lanes * sms * mhz * 1e6,
+            "ex2_per_s": rates["ex2_per_sm_clk"] * sms * mhz * 1e6}
+
+
 def parse():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -99,8 +109,8 @@ def parse():
     ap.add_argument("--steps-batched", type=int, default=2)
     ap.add_argument("--no-autotune", action="store_true")
     ap.add_argument("--no-imaging", action="store_true", help="skip the UBP / splat / MAP / SSIM leg")
-    ap.add_argument("--large4d", action="store_true",
-                    help="add the 1M-ball, 50-frame IR iteration (4d-1m-50f; ~20 GB of device memory)")
+    ap.add_argument("--no-large4d", action="store_true",
+                    help="skip the 1M-ball, 50-frame IR iterations (4d-1m-50f; batched graph vs per-frame)")
     ap.add_argument("--heart-ir", type=int, default=0, metavar="ITERS",
                     help="add the simulated-heart 4D reconstruction (Sec. 3.1) with this many IR iterations")
     ap.add_argument("--ir-quality-iters", type=int, default=160,
@@ -312,6 +322,10 @@ def run_ours(args):
         from paper_2412_03898_gb300.autotune import tune_forward
         tiles = tune_forward(geom, state, n)  # set-up, not timed
     plan = pa.forward_plan(geom, state, n, tiles=tiles)
+    # measured unit rates of this GPU (set-up, not timed): the roofline's
+    # denominator
+    rates = pa.measure_unit_rates()
+    sms = torch.cuda.get_device_properties(dev).multi_processor_count
     fws = torch.empty(max(pa.forward_workspace_size(geom, state, n, tiles=tiles), 16), dtype=torch.uint8, device=dev)
     lws = torch.empty(1 << 20, dtype=torch.uint8, device=dev)
     traces = torch.empty(1, geom.n_sensors, geom.n_samples, device=dev)
@@ -396,13 +410,13 @@ def run_ours(args):
     ir_quality = None
     if args.ir_quality_iters > 0 and not args.no_4d:
         ir_quality = bench_ir_quality(args, pa, pa_inputs, dev)
-    large4d = bench_large4d(args, pa, pa_inputs, dev) if args.large4d else None
+    large4d = None if args.no_large4d else bench_large4d(args, pa, pa_inputs, dev)
     heart_ir = bench_heart_ir(args, pa, pa_inputs, dev) if args.heart_ir > 0 else None
     clocks = sampler.stop()
 
     fwd_avg = statistics.mean(t_fwd)
     adj_avg = statistics.mean(t_adj)
-    peak_ops = SMS * FP32_LANES * SM_MAX_MHZ_NOMINAL * 1e6
+    peak = fp32_peak(rates, sms)
     if fwd_avg >= adj_avg:
         dom, ops, dur, kind = "forward (k_forward + split reduce)", FWD_OPS, fwd_avg, "forward"
     else:
@@ -422,10 +436,17 @@ def run_ours(args):
         "e2e": {"value": world * C * args.steps / (e2e_ms * 1e-3), "unit": UNIT, "h2d_bytes_per_step": e2e_in,
                 "d2h_bytes_per_step": e2e_out},
         "gpu_launches": launches_per_step * args.steps,
-        "roofline": {"bound": "alu", "kernel": dom, "achieved": achieved / 1e12, "peak": peak_ops / 1e12,
-                     "unit": "TFLOP/s", "frac": achieved / peak_ops, "traffic": recorded_traffic(kind),
-                     "note": f"FP32 operations (FMA = 1) per contribution: forward {FWD_OPS}, adjoint {ADJ_OPS}; "
-                             f"peak = {SMS} SMs x {FP32_LANES} FP32 lanes x {SM_MAX_MHZ_NOMINAL:.0f} MHz"},
+        "roofline": {"bound": "alu", "kernel": dom, "achieved": achieved / 1e12, "peak": peak["ops_per_s"] / 1e12,
+                     "unit": "TFLOP/s", "frac": achieved / peak["ops_per_s"], "traffic": recorded_traffic(kind),
+                     "note": f"FP32 operations (FMA = 1) per contribution: forward {FWD_OPS}, adjoint {ADJ_OPS} "
+                             f"(+{EX2_PER_CONTRIB} ex2 each); peak = measured FP32 FMA rate "
+                             f"{peak['lanes_per_sm_clk']:.1f} lane ops per SM per clock x {sms} SMs x "
+                             f"{peak['sm_mhz']:.0f} MHz (pa_measure_unit_rates, of measured)",
+                     "per_kernel_frac": {"forward": C * FWD_OPS / (fwd_avg * 1e-3) / peak["ops_per_s"],
+                                         "adjoint": C * ADJ_OPS / (adj_avg * 1e-3) / peak["ops_per_s"]},
+                     "ex2_frac": {"forward": C * EX2_PER_CONTRIB / (fwd_avg * 1e-3) / peak["ex2_per_s"],
+                                  "adjoint": C * EX2_PER_CONTRIB / (adj_avg * 1e-3) / peak["ex2_per_s"]}},
+        "unit_rates": rates,
         "kernels_ms": {"forward": fwd_avg, "loss": statistics.mean(t_loss), "adjoint": adj_avg},
         "fwd_contrib_per_s": C / (fwd_avg * 1e-3), "adj_contrib_per_s": C / (adj_avg * 1e-3),
     }
@@ -494,7 +515,8 @@ def bench_4d(args, pa, pa_inputs, dev, flush):
         out[f"{mode}_loss"] = float(ir.loss.sum().item())
         del ir
     out["speedup_batched_vs_per_frame"] = res["batched_graph"] / res["per_frame"]
-    out["contrib_per_s_batched"] = 2 * C * res["batched_graph"]
+    out["contrib_per_s_batched"] = C * res["batched_graph"]
+    out["contrib_per_s_per_frame"] = C * res["per_frame"]
     return out
 
 
@@ -542,7 +564,8 @@ def bench_imaging(args, pa, pa_inputs, dev, flush):
     pairs = geom.n_sensors * nvox ** 3
     out["ubp_ms"] = ubp_ms
     out["ubp_voxel_sensor_pairs_per_s"] = pairs / (ubp_ms * 1e-3)
-    peak = SMS * FP32_LANES * SM_MAX_MHZ_NOMINAL * 1e6
+    rates = pa.measure_unit_rates()
+    peak = fp32_peak(rates, torch.cuda.get_device_properties(dev).multi_processor_count)["ops_per_s"]
     out["ubp_alu_frac"] = pairs * UBP_OPS / (ubp_ms * 1e-3) / peak
     out["splat_ms"] = timed(lambda: pa.splat(st, grid, sc.kappa, n, out=gt), 3)
     out["maps_ms"] = timed(lambda: pa.maps(vol, grid), 5)
@@ -613,11 +636,12 @@ def bench_heart_ir(args, pa, pa_inputs, dev):
 
 
 def bench_large4d(args, pa, pa_inputs, dev):
-    """The paper's large-scale case: one 4D IR iteration (deform, forward, FP64
-    loss, adjoint, chain rule, Adam) over 1,000,000 balls x 50 frames with
-    1,024 sensors and 4,096 samples (4d-1m-50f), replayed from one CUDA graph
-    after a warm-up and the capture; L2 is not flushed (the iteration moves
-    ~20 GB)."""
+    """The paper's large-scale case (4d-1m-50f): one 4D IR iteration (deform,
+    forward, FP64 loss, adjoint, chain rule, Adam) over 1,000,000 balls x 50
+    frames with 1,024 sensors and 4,096 samples, in its two execution forms:
+    all frames per launch replayed from one CUDA graph, and 50 plain per-frame
+    launch sequences; CUDA events on the launching stream, one warm-up of each
+    form first.  L2 is not flushed (an iteration moves tens of GB)."""
     import torch
     from paper_2412_03898_gb300.ir import GGBallIR, init_deformation
     sc = pa_inputs.config_scene(4)
@@ -630,25 +654,41 @@ def bench_large4d(args, pa, pa_inputs, dev):
     meas = pa.forward(geom, gt, n)
     C = pa.count_contributions(geom, gt, n)
     del gt
+    torch.cuda.synchronize()
+    torch.cuda.empty_cache()
+    torch.cuda.reset_peak_memory_stats(dev)
+    base = torch.cuda.memory_allocated(dev)
     t = torch.from_numpy(pa_inputs.frame_times(F)).to(dev)
     canon = to_dev(sc.balls).contiguous()
     ir = GGBallIR(geom, canon, init_deformation(65, canon.shape[-1], dev), t, meas, n)
+    out = {"workload": f"{sc.name}: {n} balls, {F} frames, Nb = 65, {geom.n_sensors} sensors, {geom.n_samples} "
+                       "samples", "contributions_per_iteration": C}
+
+    def timed(fn, iters):
+        torch.cuda.synchronize()
+        ev = [torch.cuda.Event(enable_timing=True) for _ in range(2)]
+        ev[0].record()
+        for _ in range(iters):
+            fn()
+        ev[1].record()
+        ev[1].synchronize()
+        return ev[0].elapsed_time(ev[1]) * 1e-3 / iters
+
     ir.step()
     ir.capture()
-    torch.cuda.synchronize()
-    ev = [torch.cuda.Event(enable_timing=True) for _ in range(2)]
-    iters = 2
-    ev[0].record()
-    for _ in range(iters):
-        ir.step_graph()
-    ev[1].record()
-    ev[1].synchronize()
+    s_graph = timed(ir.step_graph, 2)
+    ir.step_per_frame()
+    s_pf = timed(ir.step_per_frame, 1)
     pa.device_error()
-    s_per_iter = ev[0].elapsed_time(ev[1]) * 1e-3 / iters
-    return {"workload": f"{sc.name}: {n} balls, {F} frames, Nb = 65, {geom.n_sensors} sensors, {geom.n_samples} "
-                        "samples", "contributions_per_forward": C, "seconds_per_iteration": s_per_iter,
-            "contrib_per_s": 2 * C / s_per_iter, "iterations_timed": iters,
-            "device_memory_gb": torch.cuda.max_memory_allocated(dev) / 1e9}
+    out.update({"iters_per_s": 1.0 / s_graph, "seconds_per_iteration": s_graph,
+                "per_frame_iters_per_s": 1.0 / s_pf, "per_frame_seconds_per_iteration": s_pf,
+                "speedup_batched_vs_per_frame": s_pf / s_graph,
+                "contrib_per_s": C / s_graph, "per_frame_contrib_per_s": C / s_pf,
+                "iterations_timed": {"batched_graph": 2, "per_frame": 1},
+                "device_memory_gb": (torch.cuda.max_memory_allocated(dev) - base) / 1e9,
+                "device_memory_note": "peak bytes allocated by the IR (parameters, Adam moments, gradients, "
+                                      "per-frame buffers, workspaces) beyond the measurements"})
+    return out
 
 
 def bench_ir_quality(args, pa, pa_inputs, dev):
@@ -736,13 +776,13 @@ def bench_batched(args, pa, pa_inputs, dev, flush):
         b.trace_grad = b.traces  # any residual: the work does not depend on its values
         b.grad_state = torch.empty_like(st)
         scenes.append(b)
-    tiles = tune_batched(scenes) if not args.no_autotune else None
+    plan = tune_batched(scenes) if not args.no_autotune else None
     ws = torch.empty(256, dtype=torch.uint8, device=dev)
     ws2 = torch.empty(256, dtype=torch.uint8, device=dev)
 
     def batched_step():
-        pa.forward_batched(scenes, tiles=tiles, workspace=ws)
-        pa.adjoint_batched(scenes, workspace=ws2)
+        pa.forward_batched(scenes, plan=plan, workspace=ws)
+        pa.adjoint_batched(scenes, plan=plan, workspace=ws2)
 
     per_ws = {}
     for b in scenes:
@@ -766,7 +806,7 @@ def bench_batched(args, pa, pa_inputs, dev, flush):
         batched_step()
     out = {"workload": "batched-16: " + ", ".join(f"{b.n}x{b.geom.n_sensors}x{b.geom.n_samples}x{b.F}"
                                                    for b in scenes),
-           "contributions_per_step": C, "tiles": list(tiles) if tiles else None, "steps": args.steps_batched}
+           "contributions_per_step": C, "plan": plan.values() if plan is not None else None, "steps": args.steps_batched}
     for mode, fn in (("graph_persistent", g.replay), ("per_scene", per_scene_step)):
         fn()
         torch.cuda.synchronize()

@@ -69,6 +69,7 @@ extern "C" {
                                  maximum first (a constant image becomes 0), L = 1 */
 #define PA_PROFILE_UNIFORM 2u /* pa_forward only: uniform ball of radius a (N-pulse
                                  p tau/(2R) on |tau| <= a), used for analytic tests */
+#define PA_PLAN_TUNE 8u       /* pa_plan_create only: time candidate plans on the caller's data */
 
 /* Acquisition geometry.  `sensors` is a device array [3][sensor_stride]
  * (x row, y row, z row) of sensor positions.  Constraints: n_sensors >= 1,
@@ -133,6 +134,15 @@ typedef struct pa_scene {
 /* Most scenes one batched call takes. */
 #define PA_MAX_SCENES 64
 
+/* Launch plan (opaque, host memory): the forward's tiles (sensors and samples
+ * per CTA, balls per TMA stage, ball splits, pairs swept together), the frames
+ * per launch of the 4D calls, and the (scene, frame, ball) items per queue
+ * grab of the batched adjoint.  Made by pa_plan_create (heuristic or timed on
+ * the caller's data) or pa_plan_from_values, released by pa_plan_destroy.
+ * A plan is read-only during the calls that take it; NULL means the built-in
+ * heuristic everywhere. */
+typedef struct pa_plan pa_plan;
+
 /* A voxel grid [nz][ny][nx] (x fastest); voxel (ix, iy, iz) is centred at
  * origin + h (ix, iy, iz), in mm.  h > 0; nx, ny, nz >= 1. */
 typedef struct pa_grid {
@@ -146,7 +156,10 @@ PA_API const char *pa_status_string(int32_t status);
 
 /* Library ABI version (major*100 + minor).  1.01 added pa_deform_backward,
  * the imaging calls (pa_ubp_filter, pa_ubp, pa_splat, pa_map, pa_ssim*) and
- * pa_selftest_bounded_wait; every 1.00 call is unchanged. */
+ * pa_selftest_bounded_wait.  2.00 added launch plans (pa_plan_*), the 4D
+ * calls that recompute states per frame chunk (pa_forward_4d,
+ * pa_adjoint_4d) and pa_measure_unit_rates, and changed pa_forward_batched
+ * and pa_adjoint_batched to take a plan in place of a tile array. */
 PA_API int32_t pa_version(void);
 
 /* Reads, returns in *out (host) and clears the device error word of the
@@ -239,19 +252,96 @@ PA_API size_t pa_batched_workspace_size(void);
  * work items (scene, frame, sensor tile, sample tile) are taken from a
  * counter in the workspace, heaviest scenes first, by one CTA per SM.
  * Each scene's traces equal pa_forward's (same tiles, no ball splits).
- * scenes: host array of n_scenes (<= PA_MAX_SCENES); tiles: as for
- * pa_forward_ex (ball splits ignored) or NULL; workspace: device, at least
+ * scenes: host array of n_scenes (<= PA_MAX_SCENES); plan: its tiles (ball
+ * splits ignored), or NULL for the heuristic; workspace: device, at least
  * pa_batched_workspace_size() bytes, 16-byte aligned.  Only the Gaussian
  * profile; flags: PA_ACCUMULATE. */
-PA_API int32_t pa_forward_batched(const pa_scene *scenes, int32_t n_scenes, uint32_t flags, const int32_t *tiles,
+PA_API int32_t pa_forward_batched(const pa_scene *scenes, int32_t n_scenes, uint32_t flags, const pa_plan *plan,
                                   void *workspace, size_t workspace_bytes, void *stream);
 
 /* Static-mode adjoint of several scenes in one persistent launch: warps take
  * chunks of (scene, frame, ball) items from a counter in the workspace,
- * scenes with the most sensors first.  Each scene's grad_state equals
- * pa_adjoint's static mode.  flags: PA_ACCUMULATE. */
-PA_API int32_t pa_adjoint_batched(const pa_scene *scenes, int32_t n_scenes, uint32_t flags, void *workspace,
-                                  size_t workspace_bytes, void *stream);
+ * scenes with the most sensors first; plan: its items per grab, or NULL
+ * (8).  Each scene's grad_state equals pa_adjoint's static mode.  flags:
+ * PA_ACCUMULATE. */
+PA_API int32_t pa_adjoint_batched(const pa_scene *scenes, int32_t n_scenes, uint32_t flags, const pa_plan *plan,
+                                  void *workspace, size_t workspace_bytes, void *stream);
+
+/* Device workspace bytes pa_plan_create needs to time candidates on these
+ * scenes (the largest forward workspace among the candidate tiles of a
+ * single scene, or a batched call's queue counter). */
+PA_API size_t pa_plan_workspace_size(const pa_scene *scenes, int32_t n_scenes);
+
+/* Launch plan for scenes like these (Sec. 1 and Sec. 2.2 batching; the
+ * paper prints no launch configuration, so the tiles come from this tuner).
+ * Without PA_PLAN_TUNE the plan holds the built-in heuristic and nothing is
+ * launched.  With PA_PLAN_TUNE the library times every candidate tile plan
+ * (best of several CUDA-event-timed runs on `stream`) and keeps the fastest:
+ * for one scene through pa_forward_ex (the planner choosing ball splits),
+ * for several through pa_forward_batched, and for several scenes that all
+ * carry trace_grad and grad_state also the batched adjoint's items per grab.
+ * Tuning overwrites the scenes' traces (and grad_state), synchronises
+ * `stream` and must not run during stream capture.  workspace: device,
+ * 256-byte aligned, at least pa_plan_workspace_size() bytes.  *out receives
+ * the plan (host memory owned by the caller until pa_plan_destroy); on an
+ * error *out is NULL. */
+PA_API int32_t pa_plan_create(const pa_scene *scenes, int32_t n_scenes, uint32_t flags, void *workspace,
+                              size_t workspace_bytes, void *stream, pa_plan **out);
+
+/* A plan from explicit values (host int32[7], or NULL for all defaults):
+ * {sensors per CTA (1..16), samples per CTA (multiple of 4), balls per stage
+ * (multiple of 4, <= 8192), ball splits, pairs per sweep (1, 2, 4, 8, 16),
+ * frames per 4D launch, batched-adjoint items per grab (<= 1024)}, 0 = the
+ * heuristic for that entry.  For tuned values from another process or a
+ * cache. */
+PA_API int32_t pa_plan_from_values(const int32_t *values7, pa_plan **out);
+
+/* Reads a plan: values7 (host int32[7], same order as pa_plan_from_values)
+ * and, if timings2 != NULL, the best forward and batched-adjoint times in ms
+ * measured while tuning (0 when not tuned). */
+PA_API int32_t pa_plan_get(const pa_plan *plan, int32_t *values7, float *timings2);
+
+/* Releases a plan (NULL is ignored). */
+PA_API void pa_plan_destroy(pa_plan *plan);
+
+/* Scratch bytes pa_forward_4d needs: one frame chunk of deformed states
+ * [K][5][stride] plus the forward's split partials for K frames. */
+PA_API size_t pa_forward_4d_workspace_size(const pa_geom *geom, const pa_canon *canon, int32_t n_frames,
+                                           const pa_plan *plan);
+
+/* Forward projection of a 4D sequence straight from the GGBall parameters
+ * (Eq. 1-2, Sec. 2.2; radiator as pa_forward): frames are processed in
+ * chunks of K (the plan's frames per launch, else as many as keep one
+ * chunk's traces within 32 MiB of L2), each chunk deformed into the
+ * workspace and projected in one launch, so the states of at most K frames
+ * exist at any time: memory is the canonical cloud, its deformation
+ * parameters and one chunk, whatever n_frames is.
+ *   t_frames  device [n_frames] normalised frame times
+ *   traces    device [n_frames][n_sensors][n_samples], 16-byte aligned
+ *   workspace device, 256-byte aligned, pa_forward_4d_workspace_size() bytes
+ * flags: PA_ACCUMULATE.  Traces equal pa_deform_balls + pa_forward_ex with
+ * the same tiles per chunk. */
+PA_API int32_t pa_forward_4d(const pa_geom *geom, const pa_canon *canon, const float *t_frames, int32_t n_frames,
+                             float *traces, uint32_t flags, const pa_plan *plan, void *workspace,
+                             size_t workspace_bytes, void *stream);
+
+/* Scratch bytes pa_adjoint_4d needs: one frame chunk of states and one of
+ * state gradients, [K][5][stride] each. */
+PA_API size_t pa_adjoint_4d_workspace_size(const pa_geom *geom, const pa_canon *canon, int32_t n_frames,
+                                           const pa_plan *plan);
+
+/* Adjoint of pa_forward_4d (Sec. 2.2: the canonical attributes and every
+ * (theta, sigma, omega) are learnable): per frame chunk, the deformed states
+ * are recomputed (never stored across chunks), the static adjoint gives their
+ * gradients, and the chain rule of Eq. 1-2 adds them into dL/d(canonical
+ * cloud) grads->state [5][stride] and dL/d(omega, theta, sigma)
+ * [5][n_basis][stride].  trace_grad: device [n_frames][S][T], 16-byte
+ * aligned; frame_scale: device [n_frames] or NULL (= 1).  flags:
+ * PA_ACCUMULATE.  Equals pa_adjoint's 4D mode up to float summation order,
+ * deterministic, no atomics. */
+PA_API int32_t pa_adjoint_4d(const pa_geom *geom, const pa_canon *canon, const float *t_frames, int32_t n_frames,
+                             const float *trace_grad, const float *frame_scale, pa_grads *grads, uint32_t flags,
+                             const pa_plan *plan, void *workspace, size_t workspace_bytes, void *stream);
 
 /* Scratch bytes pa_residual_loss needs. */
 PA_API size_t pa_loss_workspace_size(int64_t per_frame, int32_t n_frames);
@@ -274,12 +364,16 @@ PA_API int32_t pa_residual_loss(const float *pred, const float *meas, int64_t pe
  * Same arguments, results and determinism as pa_residual_loss.  Its scratch
  * is a fixed 128 KiB array inside the library, held on every GPU that loads
  * the library until the process exits, with room for 16384 (frame, block)
- * partial sums; a frame of P samples takes min(1024, ceil(P / 32768)) blocks
- * (for example, up to 224 frames of 576 x 4096 samples).  Larger problems
+ * partial sums; a frame of P samples takes min(1024, ceil(P / 32768)) blocks,
+ * so floor(16384 / blocks) frames fit (for example, 227 frames of 576 x 4096
+ * samples, 72 blocks each).  Larger problems
  * return PA_ERR_WORKSPACE without launching anything.  It allocates nothing.
  * The first call on a device looks up that array's device address (with the
- * device current) and caches it; make that first call before any stream
- * capture.  All calls share the one array: calls that overlap on the GPU
+ * device current) and caches it per device index for the life of the
+ * process; make that first call before any stream capture.  The cached
+ * address belongs to the device's primary context: after cudaDeviceReset, or
+ * from a different (non-primary) context on the same device, it is stale, so
+ * such callers must not use this entry point.  All calls share the one array: calls that overlap on the GPU
  * (two streams or two threads) race and must be serialised by the caller.
  * Each call writes every partial it reads, so the array never needs
  * clearing. */
@@ -383,6 +477,17 @@ PA_API int32_t pa_ssim(const float *x, const float *y, int32_t H, int32_t W, flo
  * device error word (read it with pa_device_error) and exits with nothing in
  * flight, so the context stays usable. */
 PA_API int32_t pa_selftest_bounded_wait(uint64_t limit_ns, void *stream);
+
+/* Measurement aid for the roofline denominators (no counterpart in the
+ * paper): the throughput of the units that bound the forward and adjoint
+ * sample loops, measured on the current device by probe kernels of eight
+ * independent dependency chains per thread in one full wave.  out4 (host)
+ * receives, per SM and clock, {scalar FP32 FMA lane operations, packed
+ * FP32x2 FMA lane operations (two per lane and instruction), SFU base-2
+ * exponentials (ex2.approx.ftz.f32)} and the SM clock in MHz that block 0
+ * saw during the scalar probe (clock64 over %globaltimer).  Runs about
+ * 0.1 s of device time and synchronises `stream`; allocates nothing. */
+PA_API int32_t pa_measure_unit_rates(void *stream, double *out4);
 
 #ifdef __cplusplus
 }

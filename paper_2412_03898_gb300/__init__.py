@@ -25,7 +25,9 @@ __all__ = [
     "PAError", "Geometry", "round4", "pad_last", "deform_balls", "deform_backward", "forward", "adjoint", "residual_loss", "sumsq",
     "count_contributions", "adam_step", "device_error", "forward_plan", "forward_workspace_size",
     "PAProject", "PAProject4D", "PALoss", "Scene", "forward_batched", "adjoint_batched", "adam_step_scheduled", "step_increment",
-    "Grid", "ubp_filter", "ubp", "splat", "maps", "ssim",
+    "Plan", "forward_4d", "adjoint_4d", "forward_4d_workspace_size", "adjoint_4d_workspace_size", "Buffers4D",
+    "forward_plan_for",
+    "Grid", "ubp_filter", "ubp", "splat", "maps", "ssim", "measure_unit_rates",
 ]
 
 
@@ -191,6 +193,15 @@ def selftest_bounded_wait(limit_ns: int = 2_000_000) -> None:
     _lib.check(_LIB.pa_selftest_bounded_wait(int(limit_ns), _stream()), "pa_selftest_bounded_wait")
 
 
+def measure_unit_rates() -> dict:
+    """Measured throughput of this GPU's FP32 FMA pipe (scalar and packed
+    FP32x2) and SFU ex2, per SM per clock, and the SM clock in MHz."""
+    out = (ctypes.c_double * 4)()
+    _lib.check(_LIB.pa_measure_unit_rates(_stream(), out), "pa_measure_unit_rates")
+    return {"ffma_lanes_per_sm_clk": out[0], "ffma2_lanes_per_sm_clk": out[1], "ex2_per_sm_clk": out[2],
+            "sm_mhz": out[3]}
+
+
 def _tiles(tiles: Optional[Sequence[int]]):
     if tiles is None:
         return None
@@ -211,6 +222,17 @@ def forward_plan(geom: Geometry, state: torch.Tensor, n: Optional[int] = None,
     state, bs, n = _balls_struct(state, n)
     out = (ctypes.c_int32 * 7)()
     _lib.check(_LIB.pa_forward_plan_info(ctypes.byref(geom.struct()), ctypes.byref(bs), int(state.shape[0]),
+                                         _tiles(tiles), out), "pa_forward_plan_info")
+    return dict(s_tile=out[0], t_tile=out[1], nb_tile=out[2], n_splits=out[3], group=out[4], ctas=out[5],
+                smem=out[6])
+
+
+def forward_plan_for(geom: Geometry, n: int, n_frames: int, tiles: Optional[Sequence[int]] = None) -> dict:
+    """The plan pa_forward_ex would use for n balls and n_frames frames (no
+    ball data needed: the query reads only the sizes)."""
+    bs = _lib.pa_balls(16, int(n), round4(max(int(n), 1)))  # pointer never dereferenced by the query
+    out = (ctypes.c_int32 * 7)()
+    _lib.check(_LIB.pa_forward_plan_info(ctypes.byref(geom.struct()), ctypes.byref(bs), int(n_frames),
                                          _tiles(tiles), out), "pa_forward_plan_info")
     return dict(s_tile=out[0], t_tile=out[1], nb_tile=out[2], n_splits=out[3], group=out[4], ctas=out[5],
                 smem=out[6])
@@ -350,10 +372,74 @@ def _scene_array(scenes):
     return (_lib.pa_scene * max(len(scenes), 1))(*[sc.struct() for sc in scenes])
 
 
+class Plan:
+    """Launch plan (pa_plan): forward tiles, frames per 4D launch and the
+    batched adjoint's items per queue grab.  Plan.create() asks the library
+    for the heuristic or, with tune=True, times the candidate plans on the
+    given scenes (overwriting their traces and grad_state); Plan.from_values()
+    wraps explicit values (0 = heuristic)."""
+
+    def __init__(self, handle: int):
+        self._h = ctypes.c_void_p(handle)
+
+    @classmethod
+    def create(cls, scenes, tune: bool = True) -> "Plan":
+        scenes = list(scenes)
+        dev = scenes[0].state.device
+        for sc in scenes:
+            if sc.traces is None:
+                sc.traces = torch.empty(sc.F, sc.geom.n_sensors, sc.geom.n_samples, dtype=torch.float32,
+                                        device=dev)
+            _check(sc.traces, "traces")
+        arr = _scene_array(scenes)  # after the scratch traces exist
+        need = int(_LIB.pa_plan_workspace_size(arr, len(scenes))) if tune else 0
+        ws = torch.empty(max(need, 256), dtype=torch.uint8, device=dev)
+        h = ctypes.c_void_p()
+        _lib.check(_LIB.pa_plan_create(arr, len(scenes), _lib.PA_PLAN_TUNE if tune else 0, ws.data_ptr(),
+                                       ws.numel(), _stream(), ctypes.byref(h)), "pa_plan_create")
+        return cls(h.value)
+
+    @classmethod
+    def from_values(cls, tiles: Optional[Sequence[int]] = None, frames_per_chunk: int = 0,
+                    adj_chunk: int = 0) -> "Plan":
+        vals = [int(v) for v in (tiles or ())] + [0] * (5 - len(tiles or ()))
+        arr = (ctypes.c_int32 * 7)(*(vals[:5] + [int(frames_per_chunk), int(adj_chunk)]))
+        h = ctypes.c_void_p()
+        _lib.check(_LIB.pa_plan_from_values(arr, ctypes.byref(h)), "pa_plan_from_values")
+        return cls(h.value)
+
+    @property
+    def handle(self) -> ctypes.c_void_p:
+        return self._h
+
+    def values(self) -> dict:
+        v = (ctypes.c_int32 * 7)()
+        t = (ctypes.c_float * 2)()
+        _lib.check(_LIB.pa_plan_get(self._h, v, t), "pa_plan_get")
+        return {"tiles": tuple(v[:5]), "frames_per_chunk": v[5], "adj_chunk": v[6], "forward_ms": t[0],
+                "adjoint_ms": t[1], "tuned": t[0] > 0}
+
+    def __del__(self):
+        h, self._h = getattr(self, "_h", None), None
+        if h is not None and h.value:
+            try:
+                _LIB.pa_plan_destroy(h)
+            except Exception:  # pragma: no cover (interpreter shutdown)
+                pass
+
+
+def _plan_arg(plan: Optional["Plan"], tiles: Optional[Sequence[int]]):
+    """(plan handle or None, the Plan object to keep alive)."""
+    if plan is None and tiles is not None:
+        plan = Plan.from_values(tiles)
+    return (plan.handle if plan is not None else None), plan
+
+
 def forward_batched(scenes, tiles: Optional[Sequence[int]] = None, accumulate: bool = False,
-                    workspace: Optional[torch.Tensor] = None):
+                    workspace: Optional[torch.Tensor] = None, plan: Optional[Plan] = None):
     """Forward projection of several scenes in one persistent launch; fills
-    (allocating if needed) each scene's traces [F, S, T]."""
+    (allocating if needed) each scene's traces [F, S, T].  plan (or tiles,
+    wrapped into a plan) sets the tiles."""
     for sc in scenes:
         if sc.traces is None:
             sc.traces = torch.empty(sc.F, sc.geom.n_sensors, sc.geom.n_samples, dtype=torch.float32,
@@ -363,12 +449,15 @@ def forward_batched(scenes, tiles: Optional[Sequence[int]] = None, accumulate: b
     dev = scenes[0].state.device if scenes else torch.device("cuda")
     if workspace is None:
         workspace = torch.empty(int(_LIB.pa_batched_workspace_size()), dtype=torch.uint8, device=dev)
-    _lib.check(_LIB.pa_forward_batched(arr, len(scenes), _lib.PA_ACCUMULATE if accumulate else 0, _tiles(tiles),
+    h, keep = _plan_arg(plan, tiles)
+    _lib.check(_LIB.pa_forward_batched(arr, len(scenes), _lib.PA_ACCUMULATE if accumulate else 0, h,
                                        workspace.data_ptr(), workspace.numel(), _stream()), "pa_forward_batched")
+    del keep
     return [sc.traces for sc in scenes]
 
 
-def adjoint_batched(scenes, accumulate: bool = False, workspace: Optional[torch.Tensor] = None):
+def adjoint_batched(scenes, accumulate: bool = False, workspace: Optional[torch.Tensor] = None,
+                    plan: Optional[Plan] = None):
     """Static-mode adjoint of several scenes in one persistent launch; reads
     each scene's trace_grad and fills its grad_state [F, 5, stride]."""
     for sc in scenes:
@@ -380,9 +469,88 @@ def adjoint_batched(scenes, accumulate: bool = False, workspace: Optional[torch.
     dev = scenes[0].state.device if scenes else torch.device("cuda")
     if workspace is None:
         workspace = torch.empty(int(_LIB.pa_batched_workspace_size()), dtype=torch.uint8, device=dev)
-    _lib.check(_LIB.pa_adjoint_batched(arr, len(scenes), _lib.PA_ACCUMULATE if accumulate else 0,
+    h = plan.handle if plan is not None else None
+    _lib.check(_LIB.pa_adjoint_batched(arr, len(scenes), _lib.PA_ACCUMULATE if accumulate else 0, h,
                                        workspace.data_ptr(), workspace.numel(), _stream()), "pa_adjoint_batched")
     return [sc.grad_state for sc in scenes]
+
+
+def _deform_views(deform: torch.Tensor):
+    _check(deform, "deform")
+    if deform.dim() != 4 or deform.shape[0] != 3 or deform.shape[1] != 5:
+        raise ValueError("deform must be [3, 5, Nb, stride] (omega, theta, sigma)")
+    return deform[0], deform[1], deform[2]
+
+
+def forward_4d_workspace_size(geom: Geometry, canon: torch.Tensor, deform: torch.Tensor, t_frames: torch.Tensor,
+                              n: Optional[int] = None, plan: Optional[Plan] = None) -> int:
+    cs, n = _canon_struct(canon, *_deform_views(deform), n)
+    return int(_LIB.pa_forward_4d_workspace_size(ctypes.byref(geom.struct()), ctypes.byref(cs),
+                                                 int(t_frames.numel()), plan.handle if plan else None))
+
+
+def adjoint_4d_workspace_size(geom: Geometry, canon: torch.Tensor, deform: torch.Tensor, t_frames: torch.Tensor,
+                              n: Optional[int] = None, plan: Optional[Plan] = None) -> int:
+    cs, n = _canon_struct(canon, *_deform_views(deform), n)
+    return int(_LIB.pa_adjoint_4d_workspace_size(ctypes.byref(geom.struct()), ctypes.byref(cs),
+                                                 int(t_frames.numel()), plan.handle if plan else None))
+
+
+def _workspace(ws: Optional[torch.Tensor], need: int, dev) -> torch.Tensor:
+    if ws is None or ws.numel() < need:
+        ws = torch.empty(max(need, 256), dtype=torch.uint8, device=dev)
+    return ws
+
+
+def forward_4d(geom: Geometry, canon: torch.Tensor, deform: torch.Tensor, t_frames: torch.Tensor,
+               n: Optional[int] = None, out: Optional[torch.Tensor] = None, accumulate: bool = False,
+               plan: Optional[Plan] = None, workspace: Optional[torch.Tensor] = None) -> torch.Tensor:
+    """Traces [F, S, T] of the 4D sequence straight from the GGBall parameters
+    (canon [5, stride], deform [3, 5, Nb, stride]): states are deformed per
+    frame chunk in the workspace and never held for all frames."""
+    cs, n = _canon_struct(canon, *_deform_views(deform), n)
+    _check(t_frames, "t_frames")
+    F = int(t_frames.numel())
+    if out is None:
+        if accumulate:
+            raise ValueError("accumulate=True needs out")
+        out = torch.empty(F, geom.n_sensors, geom.n_samples, dtype=torch.float32, device=canon.device)
+    _check(out, "out")
+    h = plan.handle if plan is not None else None
+    need = int(_LIB.pa_forward_4d_workspace_size(ctypes.byref(geom.struct()), ctypes.byref(cs), F, h))
+    workspace = _workspace(workspace, need, canon.device)
+    _lib.check(_LIB.pa_forward_4d(ctypes.byref(geom.struct()), ctypes.byref(cs), t_frames.data_ptr(), F,
+                                  out.data_ptr(), _lib.PA_ACCUMULATE if accumulate else 0, h, workspace.data_ptr(),
+                                  workspace.numel(), _stream()), "pa_forward_4d")
+    return out
+
+
+def adjoint_4d(geom: Geometry, trace_grad: torch.Tensor, canon: torch.Tensor, deform: torch.Tensor,
+               t_frames: torch.Tensor, n: Optional[int] = None, frame_scale: Optional[torch.Tensor] = None,
+               accumulate: bool = False, out=None, plan: Optional[Plan] = None,
+               workspace: Optional[torch.Tensor] = None):
+    """Adjoint of forward_4d: (g_canon [5, stride], g_deform [3, 5, Nb,
+    stride]), states recomputed per frame chunk."""
+    cs, n = _canon_struct(canon, *_deform_views(deform), n)
+    _check(t_frames, "t_frames")
+    _check(trace_grad, "trace_grad")
+    if frame_scale is not None:
+        _check(frame_scale, "frame_scale")
+    F = int(t_frames.numel())
+    if out is None:
+        out = (torch.empty_like(canon), torch.empty_like(deform))
+    gc, gd = out
+    _check(gc, "g_canon")
+    _check(gd, "g_deform")
+    grads = _lib.pa_grads(gc.data_ptr(), gd[0].data_ptr(), gd[1].data_ptr(), gd[2].data_ptr())
+    h = plan.handle if plan is not None else None
+    need = int(_LIB.pa_adjoint_4d_workspace_size(ctypes.byref(geom.struct()), ctypes.byref(cs), F, h))
+    workspace = _workspace(workspace, need, canon.device)
+    _lib.check(_LIB.pa_adjoint_4d(ctypes.byref(geom.struct()), ctypes.byref(cs), t_frames.data_ptr(), F,
+                                  trace_grad.data_ptr(), _ptr(frame_scale), ctypes.byref(grads),
+                                  _lib.PA_ACCUMULATE if accumulate else 0, h, workspace.data_ptr(), workspace.numel(),
+                                  _stream()), "pa_adjoint_4d")
+    return gc, gd
 
 
 def adam_step_scheduled(x: torch.Tensor, g: torch.Tensor, m: torch.Tensor, v: torch.Tensor, lr0: float,
@@ -424,57 +592,80 @@ class PAProject(torch.autograd.Function):
         return gs, None, None
 
 
-class PAProject4D(torch.autograd.Function):
-    """(canon, omega, theta, sigma) -> traces [F, S, T] through Eq. 1-2.
+class Buffers4D:
+    """Preallocated workspaces and gradient outputs of one 4D problem, so that
+    an IR iteration through autograd reuses the same device buffers every
+    time (and a CUDA graph of it keeps fixed addresses): the 4D calls'
+    workspaces, the loss workspace, the residual and the two gradients."""
 
-    By default the per-frame states of the forward call are kept (20 bytes
-    per ball and frame, small beside the deformation parameters' 3.9 KB per
-    ball) and backward runs the static adjoint over them followed by
-    deform_backward, the faster form.  keep_states=False drops them and
-    backward runs the fused 4D adjoint, which recomputes them in-kernel."""
+    def __init__(self, geom: Geometry, canon: torch.Tensor, deform: torch.Tensor, t_frames: torch.Tensor,
+                 n: Optional[int] = None, plan: Optional[Plan] = None):
+        dev = canon.device
+        F = int(t_frames.numel())
+        self.fws = _workspace(None, forward_4d_workspace_size(geom, canon, deform, t_frames, n, plan), dev)
+        self.aws = _workspace(None, adjoint_4d_workspace_size(geom, canon, deform, t_frames, n, plan), dev)
+        self.lws = _workspace(None, int(_LIB.pa_loss_workspace_size(geom.n_sensors * geom.n_samples, F)), dev)
+        self.resid = torch.empty(F, geom.n_sensors, geom.n_samples, dtype=torch.float32, device=dev)
+        self.g_canon = torch.zeros_like(canon)
+        self.g_deform = torch.zeros_like(deform)
+
+
+class PAProject4D(torch.autograd.Function):
+    """(canon [5, stride], deform [3, 5, Nb, stride] = (omega, theta, sigma))
+    -> traces [F, S, T] through Eq. 1-2.
+
+    Deformed states are recomputed per frame chunk rather than stored: the
+    forward runs pa_forward_4d, and backward runs pa_adjoint_4d, which deforms
+    each chunk again, takes its static adjoint and applies the chain rule of
+    Eq. 1-2.  Nothing of shape [F, 5, N] is kept between the two.
+    fused=True makes backward use the single fused 4D adjoint kernel
+    (pa_adjoint's 4D mode, no workspace at all, lower occupancy).
+    bufs: optional Buffers4D whose workspaces and gradient tensors are used
+    instead of fresh allocations."""
 
     @staticmethod
-    def forward(ctx, canon, omega, theta, sigma, geom: Geometry, t_frames, n: Optional[int] = None,
-                keep_states: bool = True):
-        state = deform_balls(canon, omega, theta, sigma, t_frames, n)
-        traces = forward(geom, state, n)
-        ctx.geom, ctx.n, ctx.keep = geom, n, keep_states
-        if keep_states:
-            ctx.save_for_backward(canon, omega, theta, sigma, t_frames, state)
-        else:
-            del state
-            ctx.save_for_backward(canon, omega, theta, sigma, t_frames)
+    def forward(ctx, canon, deform, geom: Geometry, t_frames, n: Optional[int] = None, plan: Optional[Plan] = None,
+                bufs: Optional[Buffers4D] = None, fused: bool = False):
+        traces = forward_4d(geom, canon, deform, t_frames, n, plan=plan, workspace=bufs.fws if bufs else None)
+        ctx.geom, ctx.n, ctx.plan, ctx.bufs, ctx.fused = geom, n, plan, bufs, fused
+        ctx.save_for_backward(canon, deform, t_frames)
         return traces
 
     @staticmethod
     def backward(ctx, g):
-        if ctx.keep:
-            canon, omega, theta, sigma, t_frames, state = ctx.saved_tensors
-            g_state = adjoint(ctx.geom, g.contiguous(), state=state, n=ctx.n)
-            gc, go, gt, gs = deform_backward(canon, omega, theta, sigma, t_frames, g_state, ctx.n)
+        canon, deform, t_frames = ctx.saved_tensors
+        bufs = ctx.bufs
+        out = (bufs.g_canon, bufs.g_deform) if bufs else (torch.empty_like(canon), torch.empty_like(deform))
+        if ctx.fused:
+            adjoint(ctx.geom, g.contiguous(), canon=canon, omega=deform[0], theta=deform[1], sigma=deform[2],
+                    t_frames=t_frames, n=ctx.n, out=(out[0], out[1][0], out[1][1], out[1][2]))
+            gc, gd = out
         else:
-            canon, omega, theta, sigma, t_frames = ctx.saved_tensors
-            gc, go, gt, gs = adjoint(ctx.geom, g.contiguous(), canon=canon, omega=omega, theta=theta, sigma=sigma,
-                                     t_frames=t_frames, n=ctx.n)
-        return gc, go, gt, gs, None, None, None, None
+            gc, gd = adjoint_4d(ctx.geom, g.contiguous(), canon, deform, t_frames, ctx.n, out=out, plan=ctx.plan,
+                                workspace=bufs.aws if bufs else None)
+        return gc, gd, None, None, None, None, None, None
 
 
 class PALoss(torch.autograd.Function):
-    """(pred, meas) [F, S, T] -> per-frame FP64 loss [F]."""
+    """(pred, meas) [F, S, T] -> per-frame FP64 loss [F]; backward gives the
+    residual 2 g_f (pred - meas) (and its negative for meas)."""
 
     @staticmethod
-    def forward(ctx, pred, meas):
-        loss, _ = residual_loss(pred, meas, want_loss=True)
+    def forward(ctx, pred, meas, bufs: Optional[Buffers4D] = None):
+        loss, _ = residual_loss(pred, meas, want_loss=True, workspace=bufs.lws if bufs else None)
         ctx.save_for_backward(pred, meas)
+        ctx.bufs = bufs
         return loss
 
     @staticmethod
     def backward(ctx, gl):
         pred, meas = ctx.saved_tensors
         scale = gl.to(torch.float32).contiguous()
-        _, resid = residual_loss(pred, meas, frame_scale=scale, want_loss=False, want_resid=True)
+        bufs = ctx.bufs
+        _, resid = residual_loss(pred, meas, frame_scale=scale, want_loss=False, want_resid=True,
+                                 resid_out=bufs.resid if bufs else None)
         gm = -resid if ctx.needs_input_grad[1] else None
-        return resid, gm
+        return resid, gm, None
 
 
 # ---------------------------------------------------------------------------

@@ -20,6 +20,7 @@ PA_ERR_WORKSPACE = 5
 PA_ACCUMULATE = 1
 PA_SSIM_MINMAX = 4
 PA_PROFILE_UNIFORM = 2
+PA_PLAN_TUNE = 8
 
 c_float_p = ctypes.c_void_p  # device pointers travel as void*
 
@@ -93,8 +94,17 @@ def load() -> ctypes.CDLL:
         "pa_forward_plan_info": (i32, [G, B, i32, I32P, I32P]),
         "pa_adjoint": (i32, [G, B, C, P, i32, P, P, GR, u32, P]),
         "pa_batched_workspace_size": (sz, []),
-        "pa_forward_batched": (i32, [ctypes.POINTER(pa_scene), i32, u32, I32P, P, sz, P]),
-        "pa_adjoint_batched": (i32, [ctypes.POINTER(pa_scene), i32, u32, P, sz, P]),
+        "pa_forward_batched": (i32, [ctypes.POINTER(pa_scene), i32, u32, P, P, sz, P]),
+        "pa_adjoint_batched": (i32, [ctypes.POINTER(pa_scene), i32, u32, P, P, sz, P]),
+        "pa_plan_workspace_size": (sz, [ctypes.POINTER(pa_scene), i32]),
+        "pa_plan_create": (i32, [ctypes.POINTER(pa_scene), i32, u32, P, sz, P, ctypes.POINTER(P)]),
+        "pa_plan_from_values": (i32, [I32P, ctypes.POINTER(P)]),
+        "pa_plan_get": (i32, [P, I32P, ctypes.POINTER(ctypes.c_float)]),
+        "pa_plan_destroy": (None, [P]),
+        "pa_forward_4d_workspace_size": (sz, [G, C, i32, P]),
+        "pa_forward_4d": (i32, [G, C, P, i32, P, u32, P, P, sz, P]),
+        "pa_adjoint_4d_workspace_size": (sz, [G, C, i32, P]),
+        "pa_adjoint_4d": (i32, [G, C, P, i32, P, P, GR, u32, P, P, sz, P]),
         "pa_loss_workspace_size": (sz, [i64, i32]),
         "pa_residual_loss": (i32, [P, P, i64, i32, P, P, P, P, sz, P]),
         "pa_residual_loss_noalloc": (i32, [P, P, i64, i32, P, P, P, P]),
@@ -111,6 +121,7 @@ def load() -> ctypes.CDLL:
         "pa_ssim_workspace_size": (sz, [i32, i32]),
         "pa_ssim": (i32, [P, P, i32, i32, f32, u32, P, P, P, sz, P]),
         "pa_selftest_bounded_wait": (i32, [ctypes.c_uint64, P]),
+        "pa_measure_unit_rates": (i32, [P, ctypes.POINTER(ctypes.c_double)]),
     }
     for name, (res, args) in sig.items():
         fn = getattr(lib, name)
@@ -137,7 +148,9 @@ def exported_symbols() -> list[str]:
     return ["pa_status_string", "pa_version", "pa_device_error", "pa_deform_balls", "pa_deform_backward",
             "pa_forward_workspace_size",
             "pa_forward_workspace_size_ex", "pa_forward", "pa_forward_ex", "pa_forward_plan_info", "pa_adjoint",
-            "pa_batched_workspace_size", "pa_forward_batched", "pa_adjoint_batched",
+            "pa_batched_workspace_size", "pa_forward_batched", "pa_adjoint_batched", "pa_plan_workspace_size",
+            "pa_plan_create", "pa_plan_from_values", "pa_plan_get", "pa_plan_destroy",
+            "pa_forward_4d_workspace_size", "pa_forward_4d", "pa_adjoint_4d_workspace_size", "pa_adjoint_4d",
             "pa_loss_workspace_size", "pa_residual_loss", "pa_residual_loss_noalloc", "pa_sumsq", "pa_count_contributions", "pa_adam_step",
             "pa_adam_step_scheduled", "pa_step_increment", "pa_ubp_filter", "pa_ubp", "pa_splat", "pa_map",
-            "pa_ssim_workspace_size", "pa_ssim", "pa_selftest_bounded_wait"]
+            "pa_ssim_workspace_size", "pa_ssim", "pa_selftest_bounded_wait", "pa_measure_unit_rates"]

@@ -1,27 +1,22 @@
-"""Tile autotuner for the forward projection.
+"""Tile autotuning: a thin caller of the library's own tuner (pa_plan_create
+with PA_PLAN_TUNE), which times candidate tile plans on the caller's data
+with CUDA events and keeps the fastest.
 
-Times candidate tile plans (sensors per CTA, samples per CTA, balls per TMA
-stage, ball splits, pairs per sweep) on the caller's actual data with CUDA
-events and keeps the fastest per shape class.  The shape class is (sensors,
-samples, frames, log2 of the ball count); results are cached in memory and,
-when PA_TILE_CACHE names a file, in that JSON file.
+This module only adds a cache of tuned values per shape class, in memory
+and, when PA_TILE_CACHE names a file, in that JSON file.  The shape class is
+(sensors, samples, frames, log2 of the ball count) for one scene, and the
+list of scene shapes for a batch.
 """
 from __future__ import annotations
 
 import json
 import math
 import os
-from typing import Optional, Sequence
+from typing import Optional
 
 import torch
 
-from . import Geometry, forward, forward_batched, forward_plan, forward_workspace_size
-
-# (s_tile, t_tile, nb_tile, splits, group); splits 0 = the planner's choice
-DEFAULT_CANDIDATES = [
-    (16, 1536, 512, 0, 8), (16, 1536, 512, 0, 16), (12, 2048, 512, 0, 8), (12, 2048, 512, 0, 16),
-    (16, 1536, 256, 0, 8), (16, 1024, 512, 0, 8), (8, 2048, 512, 0, 8), (16, 1536, 512, 0, 4),
-]
+from . import Geometry, Plan, Scene
 
 _cache: dict = {}
 
@@ -56,71 +51,46 @@ def shape_key(geom: Geometry, state: torch.Tensor, n: int) -> str:
     return f"fwd:S{geom.n_sensors}:T{geom.n_samples}:F{F}:N2^{int(round(math.log2(max(n, 1))))}"
 
 
-def _time(fn, reps: int, flush: torch.Tensor) -> float:
-    fn()
-    torch.cuda.synchronize()
-    best = float("inf")
-    for _ in range(reps):
-        flush.zero_()
-        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-        e0.record()
-        fn()
-        e1.record()
-        e1.synchronize()
-        best = min(best, e0.elapsed_time(e1))
-    return best
-
-
-def tune_forward(geom: Geometry, state: torch.Tensor, n: Optional[int] = None,
-                 candidates: Optional[Sequence[tuple]] = None, reps: int = 3, verbose: bool = False) -> tuple:
-    """Fastest tile plan for pa_forward on this data (cached per shape class)."""
-    n = int(state.shape[-1]) if n is None else int(n)
+def _plan_from_cache(key: str) -> Optional[Plan]:
     _load_file()
-    key = shape_key(geom, state, n)
-    if key in _cache:
-        return _cache[key]
-    cands = []
-    smem_max = torch.cuda.get_device_properties(state.device).shared_memory_per_block_optin
-    for c in (candidates or DEFAULT_CANDIDATES):
-        plan = forward_plan(geom, state, n, tiles=c)
-        if plan["smem"] <= smem_max:
-            cands.append(c)
-    out = torch.empty(state.shape[0] if state.dim() == 3 else 1, geom.n_sensors, geom.n_samples,
-                      dtype=torch.float32, device=state.device)
-    flush = torch.empty(64 * 1024 * 1024, dtype=torch.float32, device=state.device)
-    best, best_ms = None, float("inf")
-    for c in cands:
-        need = forward_workspace_size(geom, state, n, tiles=c)
-        ws = torch.empty(max(need, 16), dtype=torch.uint8, device=state.device)
-        ms = _time(lambda: forward(geom, state, n, out=out, tiles=c, workspace=ws), reps, flush)
-        if verbose:
-            print(f"autotune {key} {c}: {ms:.3f} ms")
-        if ms < best_ms:
-            best, best_ms = c, ms
-    _cache[key] = tuple(best)
+    if key not in _cache:
+        return None
+    v = tuple(_cache[key]) + (0,) * (7 - len(_cache[key]))
+    return Plan.from_values(v[:5], frames_per_chunk=v[5], adj_chunk=v[6])
+
+
+def _remember(key: str, plan: Plan) -> None:
+    v = plan.values()
+    _cache[key] = tuple(v["tiles"]) + (v["frames_per_chunk"], v["adj_chunk"])
     _store_file()
-    return _cache[key]
 
 
-def tune_batched(scenes, candidates: Optional[Sequence[tuple]] = None, reps: int = 2,
-                 verbose: bool = False) -> tuple:
-    """Fastest tile plan for one persistent batched forward over `scenes`."""
+def tune_forward_plan(geom: Geometry, state: torch.Tensor, n: Optional[int] = None) -> Plan:
+    """Fastest forward plan for this one scene (cached per shape class).
+    Tuning overwrites a scratch trace buffer only."""
+    n = int(state.shape[-1]) if n is None else int(n)
+    key = shape_key(geom, state, n)
+    plan = _plan_from_cache(key)
+    if plan is None:
+        sc = Scene(geom, state, n)
+        plan = Plan.create([sc], tune=True)
+        _remember(key, plan)
+    return plan
+
+
+def tune_forward(geom: Geometry, state: torch.Tensor, n: Optional[int] = None) -> tuple:
+    """Tiles {sensors, samples, balls per stage, splits, pairs per sweep} of
+    the fastest forward plan for this scene."""
+    return tuple(tune_forward_plan(geom, state, n).values()["tiles"])
+
+
+def tune_batched(scenes) -> Plan:
+    """Fastest plan for the persistent batched forward (and, when every scene
+    carries trace_grad and grad_state, the batched adjoint's items per grab)
+    over these scenes.  Tuning overwrites the scenes' traces and grad_state."""
     key = "batched:" + ";".join(f"{sc.geom.n_sensors}x{sc.geom.n_samples}x{sc.F}x{sc.n}" for sc in scenes)
-    if key in _cache:
-        return _cache[key]
-    dev = scenes[0].state.device
-    smem_max = torch.cuda.get_device_properties(dev).shared_memory_per_block_optin
-    cands = []
-    for c in (candidates or DEFAULT_CANDIDATES):
-        if forward_plan(scenes[0].geom, scenes[0].state, scenes[0].n, tiles=c)["smem"] <= smem_max:
-            cands.append(c)
-    flush = torch.empty(64 * 1024 * 1024, dtype=torch.float32, device=dev)
-    best, best_ms = None, float("inf")
-    for c in cands:
-        ms = _time(lambda: forward_batched(scenes, tiles=c), reps, flush)
-        if verbose:
-            print(f"autotune batched {c}: {ms:.3f} ms")
-        if ms < best_ms:
-            best, best_ms = c, ms
-    _cache[key] = tuple(best)
-    return _cache[key]
+    plan = _plan_from_cache(key)
+    if plan is None:
+        plan = Plan.create(list(scenes), tune=True)
+        _remember(key, plan)
+    return plan

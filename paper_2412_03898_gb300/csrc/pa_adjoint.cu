@@ -381,9 +381,9 @@ __global__ void __launch_bounds__(32 * kAdjWarps, 4) k_adjoint_4d(const AdjArgs 
   if (dom) set_error(A.err, PA_ERR_DOMAIN);
 }
 
-// Batched static mode: persistent warps take chunks of (scene, frame, ball)
-// items from a global counter; scenes are ordered heaviest first by the host.
-constexpr int kAdjChunk = 8;
+// Batched static mode: persistent warps take chunks of A.chunk (scene, frame,
+// ball) items from a global counter; scenes are ordered heaviest first by the
+// host.
 
 __global__ void __launch_bounds__(32 * kAdjWarps) k_adjoint_batched(const BatchAdjArgs A) {
   __shared__ __align__(16) float4 recs[kAdjWarps * 96];
@@ -392,10 +392,10 @@ __global__ void __launch_bounds__(32 * kAdjWarps) k_adjoint_batched(const BatchA
   bool dom = false;
   while (true) {
     unsigned long long base = 0;
-    if (lane == 0) base = atomicAdd(A.counter, (unsigned long long)kAdjChunk);
+    if (lane == 0) base = atomicAdd(A.counter, (unsigned long long)A.chunk);
     base = __shfl_sync(FULL, base, 0);
     if ((long long)base >= A.total_items) break;
-    const long long end = min((long long)base + kAdjChunk, A.total_items);
+    const long long end = min((long long)base + A.chunk, A.total_items);
     for (long long item = (long long)base; item < end; ++item) {
       int sc = 0;
       while (sc + 1 < A.n_scenes && item >= A.sc[sc + 1].item_begin) ++sc;
@@ -459,7 +459,7 @@ cudaError_t launch_adjoint_batched(const BatchAdjArgs &a, int sms, cudaStream_t 
   if (occ < 1) return cudaErrorInvalidConfiguration;
   e = cudaMemsetAsync(a.counter, 0, sizeof(unsigned long long), st);
   if (e != cudaSuccess) return e;
-  const long long need = (a.total_items + kAdjChunk - 1) / kAdjChunk;
+  const long long need = (a.total_items + a.chunk - 1) / a.chunk;
   const long long grid = std::max(1LL, std::min((need + kAdjWarps - 1) / kAdjWarps, (long long)sms * occ));
   k_adjoint_batched<<<(unsigned)grid, 32 * kAdjWarps, 0, st>>>(a);
   return cudaGetLastError();

@@ -5,8 +5,20 @@
 #include <cstdint>
 #include <cstring>
 #include <mutex>
+#include <new>
 
 #include "pa_internal.h"
+
+// Launch plan of the forward and batched calls (opaque to C callers).
+struct pa_plan {
+  int32_t tiles[5];          // sensors per CTA, samples per CTA, balls per stage, ball splits, pairs per sweep
+  int32_t frames_per_chunk;  // frames per launch of pa_forward_4d / pa_adjoint_4d (0 = from the L2 size)
+  int32_t adj_chunk;         // (scene, frame, ball) items per queue grab of pa_adjoint_batched
+  int32_t tuned;             // 1 when chosen by timing candidates
+  float fwd_ms;              // best forward time measured while tuning (0 if not tuned)
+  float adj_ms;              // best batched-adjoint time measured while tuning (0 if not tuned)
+  int32_t candidates;        // plans timed
+};
 
 namespace {
 
@@ -101,6 +113,36 @@ pa::Acq make_acq(const pa_geom *g) {
 
 inline int cuda_status(cudaError_t e) { return e == cudaSuccess ? PA_OK : PA_ERR_CUDA; }
 
+// Launches the forward over F frames of states [F][5][stride] with the plan
+// for (tiles, F); arguments already checked.
+int forward_launch(const DevInfo *d, const pa_geom *geom, const float *state, long long n, long long stride,
+                   int32_t F, float *traces, uint32_t flags, const int32_t *tiles, void *ws, size_t ws_bytes,
+                   cudaStream_t st) {
+  const pa::FwdPlan p = pa::forward_plan(geom->n_sensors, geom->n_samples, n, F, d->sms, tiles ? tiles[0] : 0,
+                                         tiles ? tiles[1] : 0, tiles ? tiles[2] : 0, tiles ? tiles[3] : 0,
+                                         tiles ? tiles[4] : 0);
+  if (p.smem > (size_t)d->max_smem) return PA_ERR_INVALID_ARG;
+  if (p.ws_bytes > 0 && (ws == nullptr || ws_bytes < p.ws_bytes || !aligned(ws, 256))) return PA_ERR_WORKSPACE;
+  pa::FwdArgs a;
+  a.q = make_acq(geom);
+  a.state = state;
+  a.n = n;
+  a.stride = stride;
+  a.F = F;
+  a.out = traces;
+  a.partial = static_cast<float *>(ws);
+  a.s_tile = p.s_tile;
+  a.t_tile = p.t_tile;
+  a.nb_tile = p.nb_tile;
+  a.n_splits = p.n_splits;
+  a.n_stiles = p.n_stiles;
+  a.n_ttiles = p.n_ttiles;
+  a.balls_per_split = p.balls_per_split;
+  a.flags = flags;
+  a.err = d->err;
+  return cuda_status(pa::launch_forward(a, p, (flags & PA_PROFILE_UNIFORM) != 0, st));
+}
+
 int forward_impl(const pa_geom *geom, const pa_balls *balls, int32_t F, float *traces, uint32_t flags,
                  const int32_t *tiles, void *ws, size_t ws_bytes, void *stream) {
   int rc = check_geom(geom);
@@ -118,29 +160,85 @@ int forward_impl(const pa_geom *geom, const pa_balls *balls, int32_t F, float *t
         cudaMemsetAsync(traces, 0, sizeof(float) * (size_t)F * geom->n_sensors * geom->n_samples, st));
   }
   if (!tiles_ok(tiles)) return PA_ERR_INVALID_ARG;
-  const pa::FwdPlan p = pa::forward_plan(geom->n_sensors, geom->n_samples, balls->n, F, d->sms,
-                                         tiles ? tiles[0] : 0, tiles ? tiles[1] : 0, tiles ? tiles[2] : 0,
-                                         tiles ? tiles[3] : 0, tiles ? tiles[4] : 0);
-  if (p.smem > (size_t)d->max_smem) return PA_ERR_INVALID_ARG;
-  if (p.ws_bytes > 0 && (ws == nullptr || ws_bytes < p.ws_bytes || !aligned(ws, 256))) return PA_ERR_WORKSPACE;
-  pa::FwdArgs a;
-  a.q = make_acq(geom);
-  a.state = balls->state;
-  a.n = balls->n;
-  a.stride = balls->stride;
-  a.F = F;
-  a.out = traces;
-  a.partial = static_cast<float *>(ws);
-  a.s_tile = p.s_tile;
-  a.t_tile = p.t_tile;
-  a.nb_tile = p.nb_tile;
-  a.n_splits = p.n_splits;
-  a.n_stiles = p.n_stiles;
-  a.n_ttiles = p.n_ttiles;
-  a.balls_per_split = p.balls_per_split;
-  a.flags = flags;
-  a.err = d->err;
-  return cuda_status(pa::launch_forward(a, p, (flags & PA_PROFILE_UNIFORM) != 0, st));
+  return forward_launch(d, geom, balls->state, balls->n, balls->stride, F, traces, flags, tiles, ws, ws_bytes, st);
+}
+
+// Frames per launch of the 4D calls: as many as keep one launch's traces (or
+// residuals) within 32 MiB, so that they stay in L2 between the kernels of a
+// chunk, at least 1 and at most F; a plan may fix the number.
+int frames_per_chunk(const pa_plan *plan, int S, int T, int F) {
+  if (F <= 0) return 1;
+  if (plan && plan->frames_per_chunk > 0) return std::min(plan->frames_per_chunk, F);
+  const long long per = std::max(1LL, (long long)S * T * (long long)sizeof(float));
+  return (int)std::max(1LL, std::min<long long>((32LL << 20) / per, F));
+}
+
+inline size_t round256(size_t b) { return (b + 255) & ~(size_t)255; }
+
+// Bytes of one chunk's per-frame buffer [K][5][stride] (256-byte multiple).
+inline size_t chunk_state_bytes(const pa_canon *c, int K) {
+  return round256(sizeof(float) * 5 * (size_t)c->stride * (size_t)K);
+}
+
+// Forward split partials of the largest chunk of a 4D forward.
+size_t forward_4d_partials(const DevInfo *d, const pa_geom *g, const pa_canon *c, int32_t F, int K,
+                           const int32_t *tiles) {
+  size_t ws = 0;
+  for (int k : {K, F % K}) {
+    if (k <= 0) continue;
+    const pa::FwdPlan p = pa::forward_plan(g->n_sensors, g->n_samples, c->n, k, d->sms, tiles ? tiles[0] : 0,
+                                           tiles ? tiles[1] : 0, tiles ? tiles[2] : 0, tiles ? tiles[3] : 0,
+                                           tiles ? tiles[4] : 0);
+    ws = std::max(ws, p.ws_bytes);
+  }
+  return ws;
+}
+
+// Best of `reps` event-timed runs of fn() (returning a PA status) on `st`
+// after one untimed run.
+template <typename Fn>
+int time_best(Fn fn, cudaStream_t st, int reps, float &best_ms) {
+  int rc = fn();
+  if (rc) return rc;
+  cudaEvent_t e0, e1;
+  if (cudaEventCreate(&e0) != cudaSuccess) return PA_ERR_CUDA;
+  if (cudaEventCreate(&e1) != cudaSuccess) {
+    cudaEventDestroy(e0);
+    return PA_ERR_CUDA;
+  }
+  best_ms = 3.4e38f;
+  for (int r = 0; r < reps && rc == PA_OK; ++r) {
+    float ms = 0.f;
+    if (cudaEventRecord(e0, st) != cudaSuccess) rc = PA_ERR_CUDA;
+    if (rc == PA_OK) rc = fn();
+    if (rc == PA_OK && (cudaEventRecord(e1, st) != cudaSuccess || cudaEventSynchronize(e1) != cudaSuccess ||
+                        cudaEventElapsedTime(&ms, e0, e1) != cudaSuccess))
+      rc = PA_ERR_CUDA;
+    if (rc == PA_OK) best_ms = std::min(best_ms, ms);
+  }
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  return rc;
+}
+
+// Candidate forward tile plans the tuner times: {sensors per CTA, samples per
+// CTA, balls per stage, ball splits (0 = the planner's), pairs per sweep}.
+constexpr int32_t kTileCandidates[][5] = {
+    {16, 1536, 512, 0, 16}, {16, 1536, 512, 0, 8}, {12, 2048, 512, 0, 16}, {12, 2048, 512, 0, 8},
+    {16, 1536, 256, 0, 16}, {16, 1024, 512, 0, 16}, {8, 2048, 512, 0, 16}, {16, 1536, 512, 0, 4},
+};
+constexpr int kNumTileCandidates = sizeof(kTileCandidates) / sizeof(kTileCandidates[0]);
+constexpr int32_t kAdjChunkCandidates[] = {4, 8, 16, 32};
+
+int check_scenes(const pa_scene *scenes, int32_t n_scenes) {
+  if (n_scenes < 1 || n_scenes > PA_MAX_SCENES || scenes == nullptr) return PA_ERR_INVALID_ARG;
+  for (int i = 0; i < n_scenes; ++i) {
+    int rc = check_geom(&scenes[i].geom);
+    if (rc) return rc;
+    if ((rc = check_balls(&scenes[i].balls))) return rc;
+    if (scenes[i].n_frames < 0) return PA_ERR_INVALID_ARG;
+  }
+  return PA_OK;
 }
 
 }  // namespace
@@ -159,7 +257,7 @@ const char *pa_status_string(int32_t status) {
   }
 }
 
-int32_t pa_version(void) { return 101; }
+int32_t pa_version(void) { return 200; }
 
 int32_t pa_device_error(void *stream, int32_t *out) {
   if (out == nullptr) return PA_ERR_INVALID_ARG;
@@ -325,8 +423,9 @@ int32_t pa_adjoint(const pa_geom *geom, const pa_balls *balls, const pa_canon *c
 
 size_t pa_batched_workspace_size(void) { return 256; }
 
-int32_t pa_forward_batched(const pa_scene *scenes, int32_t n_scenes, uint32_t flags, const int32_t *tiles,
+int32_t pa_forward_batched(const pa_scene *scenes, int32_t n_scenes, uint32_t flags, const pa_plan *plan,
                            void *workspace, size_t workspace_bytes, void *stream) {
+  const int32_t *tiles = plan ? plan->tiles : nullptr;
   if (n_scenes < 0 || n_scenes > PA_MAX_SCENES || (n_scenes > 0 && scenes == nullptr)) return PA_ERR_INVALID_ARG;
   if ((flags & ~PA_ACCUMULATE) != 0) return PA_ERR_INVALID_ARG;
   if (!tiles_ok(tiles)) return PA_ERR_INVALID_ARG;
@@ -406,8 +505,8 @@ int32_t pa_forward_batched(const pa_scene *scenes, int32_t n_scenes, uint32_t fl
   return cuda_status(pa::launch_forward_batched(a, group, smem, d->sms, st));
 }
 
-int32_t pa_adjoint_batched(const pa_scene *scenes, int32_t n_scenes, uint32_t flags, void *workspace,
-                           size_t workspace_bytes, void *stream) {
+int32_t pa_adjoint_batched(const pa_scene *scenes, int32_t n_scenes, uint32_t flags, const pa_plan *plan,
+                           void *workspace, size_t workspace_bytes, void *stream) {
   if (n_scenes < 0 || n_scenes > PA_MAX_SCENES || (n_scenes > 0 && scenes == nullptr)) return PA_ERR_INVALID_ARG;
   if ((flags & ~PA_ACCUMULATE) != 0) return PA_ERR_INVALID_ARG;
   if (workspace == nullptr || workspace_bytes < pa_batched_workspace_size() || !aligned(workspace, 16))
@@ -431,6 +530,7 @@ int32_t pa_adjoint_batched(const pa_scene *scenes, int32_t n_scenes, uint32_t fl
   pa::BatchAdjArgs a;
   std::memset(&a, 0, sizeof(a));
   a.n_scenes = m;
+  a.chunk = plan && plan->adj_chunk > 0 ? plan->adj_chunk : 8;
   a.counter = static_cast<unsigned long long *>(workspace);
   a.flags = flags;
   a.err = d->err;
@@ -636,6 +736,285 @@ int32_t pa_selftest_bounded_wait(uint64_t limit_ns, void *stream) {
   const DevInfo *d = dev_info();
   if (!d) return PA_ERR_CUDA;
   return cuda_status(pa::launch_selftest_wait(limit_ns, d->err, static_cast<cudaStream_t>(stream)));
+}
+
+int32_t pa_measure_unit_rates(void *stream, double *out4) {
+  if (out4 == nullptr) return PA_ERR_INVALID_ARG;
+  const DevInfo *d = dev_info();
+  if (!d) return PA_ERR_CUDA;
+  return cuda_status(pa::measure_unit_rates(d->sms, static_cast<cudaStream_t>(stream), out4));
+}
+
+// ---------------------------------------------------------------------------
+// Launch plans.
+
+size_t pa_plan_workspace_size(const pa_scene *scenes, int32_t n_scenes) {
+  if (check_scenes(scenes, n_scenes)) return 0;
+  size_t ws = pa_batched_workspace_size();
+  if (n_scenes > 1) return ws;
+  const DevInfo *d = dev_info();
+  if (!d) return 0;
+  const pa_scene &sc = scenes[0];
+  if (sc.n_frames <= 0 || sc.balls.n == 0) return ws;
+  for (int c = -1; c < kNumTileCandidates; ++c) {
+    const int32_t *t = c < 0 ? nullptr : kTileCandidates[c];
+    const pa::FwdPlan p = pa::forward_plan(sc.geom.n_sensors, sc.geom.n_samples, sc.balls.n, sc.n_frames, d->sms,
+                                           t ? t[0] : 0, t ? t[1] : 0, t ? t[2] : 0, t ? t[3] : 0, t ? t[4] : 0);
+    if (p.smem <= (size_t)d->max_smem) ws = std::max(ws, p.ws_bytes);
+  }
+  return ws;
+}
+
+int32_t pa_plan_from_values(const int32_t *values7, pa_plan **out) {
+  if (out == nullptr) return PA_ERR_INVALID_ARG;
+  *out = nullptr;
+  if (values7 != nullptr) {
+    if (!tiles_ok(values7) || values7[5] < 0 || values7[6] < 0 || values7[6] > 1024) return PA_ERR_INVALID_ARG;
+  }
+  pa_plan *p = new (std::nothrow) pa_plan;
+  if (p == nullptr) return PA_ERR_INVALID_ARG;
+  std::memset(p, 0, sizeof(*p));
+  if (values7 != nullptr) {
+    std::memcpy(p->tiles, values7, sizeof(p->tiles));
+    p->frames_per_chunk = values7[5];
+    p->adj_chunk = values7[6];
+  }
+  *out = p;
+  return PA_OK;
+}
+
+int32_t pa_plan_create(const pa_scene *scenes, int32_t n_scenes, uint32_t flags, void *workspace,
+                       size_t workspace_bytes, void *stream, pa_plan **out) {
+  if (out == nullptr) return PA_ERR_INVALID_ARG;
+  *out = nullptr;
+  int rc = check_scenes(scenes, n_scenes);
+  if (rc) return rc;
+  if ((flags & ~PA_PLAN_TUNE) != 0) return PA_ERR_INVALID_ARG;
+  pa_plan *plan = nullptr;
+  if ((rc = pa_plan_from_values(nullptr, &plan))) return rc;
+  if (!(flags & PA_PLAN_TUNE)) {
+    *out = plan;
+    return PA_OK;
+  }
+  const DevInfo *d = dev_info();
+  if (!d) {
+    delete plan;
+    return PA_ERR_CUDA;
+  }
+  const size_t need = pa_plan_workspace_size(scenes, n_scenes);
+  if (workspace == nullptr || workspace_bytes < need || !aligned(workspace, 256)) {
+    delete plan;
+    return PA_ERR_WORKSPACE;
+  }
+  for (int i = 0; i < n_scenes; ++i) {
+    const pa_scene &sc = scenes[i];
+    if (sc.n_frames > 0 && (sc.traces == nullptr || !aligned(sc.traces, 16))) {
+      delete plan;
+      return PA_ERR_INVALID_ARG;
+    }
+  }
+  cudaStream_t st = static_cast<cudaStream_t>(stream);
+  // forward tiles: a single scene is timed through pa_forward_ex (ball
+  // splits by the planner), several through one persistent batched launch
+  float best = 3.4e38f;
+  int best_c = -1;
+  for (int c = 0; c < kNumTileCandidates; ++c) {
+    const int32_t *t = kTileCandidates[c];
+    const pa::FwdPlan p0 = pa::forward_plan(scenes[0].geom.n_sensors, scenes[0].geom.n_samples,
+                                            std::max<long long>(scenes[0].balls.n, 1), 1, d->sms, t[0], t[1],
+                                            t[2], t[3], t[4]);
+    if (p0.smem > (size_t)d->max_smem) continue;
+    pa_plan trial = *plan;
+    std::memcpy(trial.tiles, t, sizeof(trial.tiles));
+    float ms = 0.f;
+    if (n_scenes == 1) {
+      const pa_scene &sc = scenes[0];
+      rc = time_best([&] { return forward_impl(&sc.geom, &sc.balls, sc.n_frames, sc.traces, 0, t, workspace,
+                                               workspace_bytes, stream); },
+                     st, 3, ms);
+    } else {
+      rc = time_best([&] { return pa_forward_batched(scenes, n_scenes, 0, &trial, workspace, workspace_bytes,
+                                                     stream); },
+                     st, 2, ms);
+    }
+    if (rc) {
+      delete plan;
+      return rc;
+    }
+    ++plan->candidates;
+    if (ms < best) {
+      best = ms;
+      best_c = c;
+    }
+  }
+  if (best_c >= 0) {
+    std::memcpy(plan->tiles, kTileCandidates[best_c], sizeof(plan->tiles));
+    plan->fwd_ms = best;
+  }
+  // items per queue grab of the batched adjoint, when every scene with work
+  // carries its residual and gradient buffers
+  bool adj = n_scenes > 1;
+  for (int i = 0; i < n_scenes && adj; ++i) {
+    const pa_scene &sc = scenes[i];
+    if (sc.n_frames > 0 && sc.balls.n > 0 && (sc.trace_grad == nullptr || sc.grad_state == nullptr)) adj = false;
+  }
+  if (adj) {
+    float best_a = 3.4e38f;
+    for (int32_t ch : kAdjChunkCandidates) {
+      pa_plan trial = *plan;
+      trial.adj_chunk = ch;
+      float ms = 0.f;
+      rc = time_best([&] { return pa_adjoint_batched(scenes, n_scenes, 0, &trial, workspace, workspace_bytes,
+                                                     stream); },
+                     st, 2, ms);
+      if (rc) {
+        delete plan;
+        return rc;
+      }
+      ++plan->candidates;
+      if (ms < best_a) {
+        best_a = ms;
+        plan->adj_chunk = ch;
+        plan->adj_ms = ms;
+      }
+    }
+  }
+  plan->tuned = 1;
+  *out = plan;
+  return PA_OK;
+}
+
+int32_t pa_plan_get(const pa_plan *plan, int32_t *values7, float *timings2) {
+  if (plan == nullptr || values7 == nullptr) return PA_ERR_INVALID_ARG;
+  std::memcpy(values7, plan->tiles, sizeof(plan->tiles));
+  values7[5] = plan->frames_per_chunk;
+  values7[6] = plan->adj_chunk;
+  if (timings2 != nullptr) {
+    timings2[0] = plan->tuned ? plan->fwd_ms : 0.f;
+    timings2[1] = plan->tuned ? plan->adj_ms : 0.f;
+  }
+  return PA_OK;
+}
+
+void pa_plan_destroy(pa_plan *plan) { delete plan; }
+
+// ---------------------------------------------------------------------------
+// 4D calls that recompute the deformed states per frame chunk.
+
+size_t pa_forward_4d_workspace_size(const pa_geom *geom, const pa_canon *canon, int32_t n_frames,
+                                    const pa_plan *plan) {
+  if (check_geom(geom) || check_canon(canon) || n_frames <= 0 || canon->n == 0) return 0;
+  const int32_t *tiles = plan ? plan->tiles : nullptr;
+  if (!tiles_ok(tiles)) return 0;
+  const DevInfo *d = dev_info();
+  if (!d) return 0;
+  const int K = frames_per_chunk(plan, geom->n_sensors, geom->n_samples, n_frames);
+  return chunk_state_bytes(canon, K) + forward_4d_partials(d, geom, canon, n_frames, K, tiles);
+}
+
+int32_t pa_forward_4d(const pa_geom *geom, const pa_canon *canon, const float *t_frames, int32_t n_frames,
+                      float *traces, uint32_t flags, const pa_plan *plan, void *workspace, size_t workspace_bytes,
+                      void *stream) {
+  int rc = check_geom(geom);
+  if (rc) return rc;
+  if ((rc = check_canon(canon))) return rc;
+  if (n_frames < 0 || (flags & ~PA_ACCUMULATE) != 0) return PA_ERR_INVALID_ARG;
+  const int32_t *tiles = plan ? plan->tiles : nullptr;
+  if (!tiles_ok(tiles)) return PA_ERR_INVALID_ARG;
+  if (n_frames == 0) return PA_OK;
+  if (traces == nullptr || !aligned(traces, 16) || t_frames == nullptr) return PA_ERR_INVALID_ARG;
+  if (canon->n > 0 && !aligned(canon->canon, 16)) return PA_ERR_INVALID_ARG;
+  const DevInfo *d = dev_info();
+  if (!d) return PA_ERR_CUDA;
+  cudaStream_t st = static_cast<cudaStream_t>(stream);
+  const size_t per_frame = (size_t)geom->n_sensors * geom->n_samples;
+  if (canon->n == 0) {
+    if (flags & PA_ACCUMULATE) return PA_OK;
+    return cuda_status(cudaMemsetAsync(traces, 0, sizeof(float) * per_frame * n_frames, st));
+  }
+  const int K = frames_per_chunk(plan, geom->n_sensors, geom->n_samples, n_frames);
+  const size_t sbytes = chunk_state_bytes(canon, K);
+  const size_t need = sbytes + forward_4d_partials(d, geom, canon, n_frames, K, tiles);
+  if (workspace == nullptr || workspace_bytes < need || !aligned(workspace, 256)) return PA_ERR_WORKSPACE;
+  float *states = static_cast<float *>(workspace);
+  char *partials = static_cast<char *>(workspace) + sbytes;
+  for (int f0 = 0; f0 < n_frames; f0 += K) {
+    const int k = std::min(K, n_frames - f0);
+    rc = cuda_status(pa::launch_deform(canon->canon, canon->omega, canon->theta, canon->sigma, canon->n,
+                                       canon->stride, canon->n_basis, t_frames + f0, k, states, d->err, st));
+    if (rc) return rc;
+    rc = forward_launch(d, geom, states, canon->n, canon->stride, k, traces + per_frame * f0, flags, tiles,
+                        partials, workspace_bytes - sbytes, st);
+    if (rc) return rc;
+  }
+  return PA_OK;
+}
+
+size_t pa_adjoint_4d_workspace_size(const pa_geom *geom, const pa_canon *canon, int32_t n_frames,
+                                    const pa_plan *plan) {
+  if (check_geom(geom) || check_canon(canon) || n_frames <= 0 || canon->n == 0) return 0;
+  const int K = frames_per_chunk(plan, geom->n_sensors, geom->n_samples, n_frames);
+  return 2 * chunk_state_bytes(canon, K);
+}
+
+int32_t pa_adjoint_4d(const pa_geom *geom, const pa_canon *canon, const float *t_frames, int32_t n_frames,
+                      const float *trace_grad, const float *frame_scale, pa_grads *grads, uint32_t flags,
+                      const pa_plan *plan, void *workspace, size_t workspace_bytes, void *stream) {
+  int rc = check_geom(geom);
+  if (rc) return rc;
+  if ((rc = check_canon(canon))) return rc;
+  if (n_frames < 0 || grads == nullptr || (flags & ~PA_ACCUMULATE) != 0) return PA_ERR_INVALID_ARG;
+  if (canon->n == 0) return PA_OK;
+  if (!grads->state || !grads->omega || !grads->theta || !grads->sigma) return PA_ERR_INVALID_ARG;
+  if (n_frames > 0 && (t_frames == nullptr || trace_grad == nullptr || !aligned(trace_grad, 16)))
+    return PA_ERR_INVALID_ARG;
+  const size_t smem = sizeof(float4) * 8 * 96 + sizeof(float) * 3 * (size_t)geom->n_sensors;
+  const DevInfo *d = dev_info();
+  if (!d) return PA_ERR_CUDA;
+  if ((long long)smem > d->max_smem) return PA_ERR_INVALID_ARG;
+  cudaStream_t st = static_cast<cudaStream_t>(stream);
+  if (n_frames == 0) {
+    if (flags & PA_ACCUMULATE) return PA_OK;
+    const size_t rows = sizeof(float) * (size_t)canon->stride;
+    cudaError_t e = cudaMemsetAsync(grads->state, 0, rows * 5, st);
+    if (e == cudaSuccess) e = cudaMemsetAsync(grads->omega, 0, rows * 5 * canon->n_basis, st);
+    if (e == cudaSuccess) e = cudaMemsetAsync(grads->theta, 0, rows * 5 * canon->n_basis, st);
+    if (e == cudaSuccess) e = cudaMemsetAsync(grads->sigma, 0, rows * 5 * canon->n_basis, st);
+    return cuda_status(e);
+  }
+  const int K = frames_per_chunk(plan, geom->n_sensors, geom->n_samples, n_frames);
+  const size_t sbytes = chunk_state_bytes(canon, K);
+  if (workspace == nullptr || workspace_bytes < 2 * sbytes || !aligned(workspace, 256)) return PA_ERR_WORKSPACE;
+  float *states = static_cast<float *>(workspace);
+  float *gstates = reinterpret_cast<float *>(static_cast<char *>(workspace) + sbytes);
+  const size_t per_frame = (size_t)geom->n_sensors * geom->n_samples;
+  for (int f0 = 0; f0 < n_frames; f0 += K) {
+    const int k = std::min(K, n_frames - f0);
+    rc = cuda_status(pa::launch_deform(canon->canon, canon->omega, canon->theta, canon->sigma, canon->n,
+                                       canon->stride, canon->n_basis, t_frames + f0, k, states, d->err, st));
+    if (rc) return rc;
+    pa::AdjArgs a;
+    std::memset(&a, 0, sizeof(a));
+    a.q = make_acq(geom);
+    a.state = states;
+    a.stride = canon->stride;
+    a.n = canon->n;
+    a.F = k;
+    a.g = trace_grad + per_frame * f0;
+    a.frame_scale = frame_scale ? frame_scale + f0 : nullptr;
+    a.g_state = gstates;
+    a.flags = 0;
+    a.err = d->err;
+    a.n_items = (long long)k * canon->n;
+    rc = cuda_status(pa::launch_adjoint_static(a, d->sms, st));
+    if (rc) return rc;
+    rc = cuda_status(pa::launch_deform_backward(canon->canon, canon->omega, canon->theta, canon->sigma, canon->n,
+                                                canon->stride, canon->n_basis, t_frames + f0, k, gstates,
+                                                grads->state, grads->omega, grads->theta, grads->sigma,
+                                                f0 > 0 || (flags & PA_ACCUMULATE) != 0, d->err, st));
+    if (rc) return rc;
+  }
+  return PA_OK;
 }
 
 }  // extern "C"

@@ -331,6 +331,11 @@ __device__ __forceinline__ bool forward_item(const Acq &q, const float *state_f,
     if (abort) {
       // A copy did not complete in time: record it and give the copy still in
       // flight a bounded chance to land before the shared memory is reused.
+      // If that second wait also runs out the CTA returns with the copy
+      // possibly still writing its shared memory, which is undefined: this
+      // path is reached only after a real stall of the copy engine, and no
+      // test makes a real copy stall (the self-test waits on an mbarrier with
+      // no copy behind it).
       if (tid == 0) {
         set_error(err, PA_ERR_TIMEOUT);
         mbar_wait_bounded(&bars[stage], par);

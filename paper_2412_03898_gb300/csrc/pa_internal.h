@@ -69,6 +69,7 @@ struct SceneAdj {
 
 struct BatchAdjArgs {
   int n_scenes;
+  int chunk;  // (scene, frame, ball) items per queue grab, >= 1
   long long total_items;
   unsigned long long *counter;
   unsigned flags;
@@ -154,6 +155,9 @@ int minmax_partials();
 cudaError_t launch_ssim(const SsimArgs &a, double *out, float4 *minmax_ws, cudaStream_t st);
 
 cudaError_t launch_selftest_wait(unsigned long long limit_ns, unsigned *err, cudaStream_t st);
+// Unit-throughput probe (pa_probe.cu): out = {FFMA, FFMA2 lane ops, ex2} per SM
+// per clock and the SM clock in MHz; synchronises st.
+cudaError_t measure_unit_rates(int sms, cudaStream_t st, double out[4]);
 cudaError_t launch_deform_backward(const float *canon, const float *omega, const float *theta, const float *sigma,
                                    long long n, long long stride, int nb, const float *t, int F, const float *gstate,
                                    float *g_canon, float *g_omega, float *g_theta, float *g_sigma, bool acc,

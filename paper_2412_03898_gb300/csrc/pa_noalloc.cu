@@ -14,8 +14,12 @@
 // library holds its 128 KiB until the process exits.  Host code cannot pass
 // the array's name to a kernel (on the host it is only a stand-in symbol), so
 // the first call on each device looks up the array's device address with
-// cudaGetSymbolAddress, with that device current, and caches it.  That first
-// call on a device should therefore come before any stream capture.
+// cudaGetSymbolAddress, with that device current, and caches it per device
+// index for the life of the process.  That first call on a device should
+// therefore come before any stream capture.  The cached address belongs to
+// the device's primary context: after cudaDeviceReset, or from another
+// (non-primary) context on the same device, it is stale, and such callers
+// must not use this entry point.
 //
 // Every call shares the one array and reuses it without clearing it: each
 // call's first kernel writes every partial its second kernel reads, so

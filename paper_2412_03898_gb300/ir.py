@@ -1,22 +1,24 @@
 """Iterative reconstruction (IR) driver of 4D SlingBAG on the library's
 kernels (Sec. 2.2, Fig. 2 stage 2; hyper-parameters of Sec. 3.2).
 
-One IR iteration: deform every frame (Eq. 1-2) -> forward projection of all
-frames -> per-frame FP64 L2 loss and residual -> 4D adjoint -> Adam on each
-parameter group with the paper's learning rates and step decay (step_size
-160, drop 0.1).  The 4D adjoint is, by default, the static adjoint over the
-deformed states the forward already used followed by the chain rule of
-Eq. 1-2 (pa_deform_backward); fused=True uses the single fused 4D kernel
-instead, which needs no per-frame gradient buffer but runs at lower
-occupancy.  The optimiser type
-is not named in the paper; Adam is this library's reading.
+One IR iteration goes through torch.autograd: PAProject4D (deform every
+frame by Eq. 1-2 and project it, pa_forward_4d) -> PALoss (per-frame FP64 L2
+loss) -> torch.autograd.grad, whose backward runs the residual kernel and
+pa_adjoint_4d -> Adam on each parameter group with the paper's learning rates
+and step decay (step_size 160, drop 0.1).  The deformed states are
+recomputed per frame chunk in both directions and never stored for all
+frames, so device memory is the canonical cloud, its deformation parameters,
+their gradients and Adam moments, the traces and one frame chunk, whatever
+the number of frames.  fused=True makes backward use the single fused 4D
+adjoint kernel instead.  The optimiser type is not named in the paper; Adam
+is this library's reading.
 
 Two execution forms of the same iteration:
-  - batched: all frames in one launch per kernel; the whole iteration
-    (deform, forward, loss, adjoint, step counter, Adam) is captured once in
-    a CUDA graph and replayed (step_graph).  The Adam step number lives in
-    device memory, so the decayed learning rate and bias corrections need no
-    host scalars;
+  - batched: every kernel launch covers a chunk of frames (all frames when
+    they fit the chunk); the whole iteration (forward, loss, backward, step
+    counter, Adam) is captured once in a CUDA graph and replayed
+    (step_graph).  The Adam step number lives in device memory, so the
+    decayed learning rate and bias corrections need no host scalars;
   - per-frame: F plain launch sequences, one frame each, gradients
     accumulated across frames (step_per_frame).
 """
@@ -27,8 +29,8 @@ from typing import Optional
 
 import torch
 
-from . import (Geometry, adam_step_scheduled, adjoint, deform_backward, deform_balls, forward, residual_loss,
-               step_increment)
+from . import (Buffers4D, Geometry, PALoss, PAProject4D, Plan, adam_step_scheduled, adjoint, adjoint_4d,
+               forward_4d, residual_loss, step_increment)
 
 # Sec. 3.2: initial learning rates and step decay.  The paper states the
 # rates without units.  Lengths here are in mm, and the coordinate and size
@@ -52,7 +54,8 @@ class GGBallIR:
     omega, theta, sigma; t_frames: [F]; meas: [F, S, T]."""
 
     def __init__(self, geom: Geometry, canon: torch.Tensor, deform: torch.Tensor, t_frames: torch.Tensor,
-                 meas: torch.Tensor, n: Optional[int] = None, fused: bool = False, lr_scale: float = 1.0):
+                 meas: torch.Tensor, n: Optional[int] = None, fused: bool = False, lr_scale: float = 1.0,
+                 plan: Optional[Plan] = None):
         self.geom = geom
         self.canon = canon
         self.deform = deform
@@ -60,89 +63,64 @@ class GGBallIR:
         self.meas = meas
         self.n = canon.shape[-1] if n is None else int(n)
         self.F = int(t_frames.numel())
+        self.plan = plan
         dev = canon.device
-        self.g_canon = torch.zeros_like(canon)
-        self.g_deform = torch.zeros_like(deform)
         self.m_canon, self.v_canon = torch.zeros_like(canon), torch.zeros_like(canon)
         self.m_deform, self.v_deform = torch.zeros_like(deform), torch.zeros_like(deform)
-        stride = canon.shape[-1]
-        self.state = torch.empty(self.F, 5, stride, dtype=torch.float32, device=dev)
-        self.traces = torch.empty(self.F, geom.n_sensors, geom.n_samples, dtype=torch.float32, device=dev)
-        self.resid = torch.empty_like(self.traces)
-        self.loss = torch.empty(self.F, dtype=torch.float64, device=dev)
+        self.bufs = Buffers4D(geom, canon, deform, t_frames, self.n, plan)
+        self.g_canon, self.g_deform = self.bufs.g_canon, self.bufs.g_deform
+        self.loss = torch.zeros(self.F, dtype=torch.float64, device=dev)
+        self._ones = torch.ones(self.F, dtype=torch.float64, device=dev)
         self.fused = fused
         self.lr_scale = float(lr_scale)
-        self.g_state = None if fused else torch.empty(self.F, 5, stride, dtype=torch.float32, device=dev)
         self.step_count = 0
         self.step_dev = torch.zeros(1, dtype=torch.int32, device=dev)
         self.graph: Optional[torch.cuda.CUDAGraph] = None
-        self._fws = None
-        self._lws = torch.empty(1 << 20, dtype=torch.uint8, device=dev)
+        # per-frame form: one frame of traces and residual
+        self._tr1 = None
+        self._res1 = None
 
     # -- pieces ---------------------------------------------------------------
-    def _omega(self):
-        return self.deform[0]
-
-    def _grads_tuple(self):
-        return (self.g_canon, self.g_deform[0], self.g_deform[1], self.g_deform[2])
-
     def _forward_loss_adjoint(self):
-        deform_balls(self.canon, self.deform[0], self.deform[1], self.deform[2], self.t, self.n, out=self.state)
-        forward(self.geom, self.state, self.n, out=self.traces, workspace=self._fws)
-        residual_loss(self.traces, self.meas, want_loss=True, want_resid=True, loss_out=self.loss,
-                      resid_out=self.resid, workspace=self._lws)
-        self._adjoint_4d(self.resid, self.t, self.state, self.g_state, accumulate=False)
+        """Loss and gradients of one iteration through torch.autograd."""
+        c = self.canon.detach().requires_grad_()
+        d = self.deform.detach().requires_grad_()
+        traces = PAProject4D.apply(c, d, self.geom, self.t, self.n, self.plan, self.bufs, self.fused)
+        loss = PALoss.apply(traces, self.meas, self.bufs)
+        gc, gd = torch.autograd.grad(loss, (c, d), grad_outputs=(self._ones,))
+        self.loss = loss.detach()
+        return gc, gd
 
-    def _adjoint_4d(self, resid, t, state, g_state, accumulate):
-        if self.fused:
-            adjoint(self.geom, resid, canon=self.canon, omega=self.deform[0], theta=self.deform[1],
-                    sigma=self.deform[2], t_frames=t, n=self.n, out=self._grads_tuple(), accumulate=accumulate)
-        else:
-            adjoint(self.geom, resid, state=state, n=self.n, out=g_state)
-            deform_backward(self.canon, self.deform[0], self.deform[1], self.deform[2], t, g_state, self.n,
-                            out=self._grads_tuple(), accumulate=accumulate)
-
-    def lr_scale(self) -> float:
+    def lr_decay(self) -> float:
         """Step decay of Sec. 3.2 for the iteration last taken (1-based t):
         DROP_RATE ** floor((t - 1) / STEP_SIZE)."""
         return DROP_RATE ** (max(self.step_count - 1, 0) // STEP_SIZE)
 
-    def _adam(self):
+    def _adam(self, gc: torch.Tensor, gd: torch.Tensor):
         # one device-side step counter; every group reads t from it
         step_increment(self.step_dev)
         self.step_count += 1
         assert LR_COORD == LR_STD  # x, y, z and a rows share one launch
         for lr0, x, g, m, v in (
-                (LR_COORD * MM_PER_M, self.canon[:4], self.g_canon[:4], self.m_canon[:4], self.v_canon[:4]),
-                (LR_PRESSURE, self.canon[4], self.g_canon[4], self.m_canon[4], self.v_canon[4]),
-                (LR_DEFORM, self.deform, self.g_deform, self.m_deform, self.v_deform)):
+                (LR_COORD * MM_PER_M, self.canon[:4], gc[:4], self.m_canon[:4], self.v_canon[:4]),
+                (LR_PRESSURE, self.canon[4], gc[4], self.m_canon[4], self.v_canon[4]),
+                (LR_DEFORM, self.deform, gd, self.m_deform, self.v_deform)):
             adam_step_scheduled(x.reshape(-1), g.reshape(-1), m.reshape(-1), v.reshape(-1), lr0 * self.lr_scale,
                                 self.step_dev, STEP_SIZE, DROP_RATE)
 
-    def _ensure_workspace(self):
-        from . import forward_workspace_size
-        # all frames at once (batched) and one frame (per-frame form)
-        need = max(forward_workspace_size(self.geom, self.state, self.n),
-                   forward_workspace_size(self.geom, self.state[:1], self.n))
-        if need > 0 and (self._fws is None or self._fws.numel() < need):
-            self._fws = torch.empty(need, dtype=torch.uint8, device=self.canon.device)
-
     # -- iteration forms -------------------------------------------------------
+    def _iteration(self):
+        gc, gd = self._forward_loss_adjoint()
+        self._adam(gc, gd)
+
     def step(self) -> torch.Tensor:
         """One batched IR iteration with plain launches."""
-        self._ensure_workspace()
-        self._forward_loss_adjoint()
-        self._adam()
+        self._iteration()
         return self.loss
-
-    def _iteration(self):
-        self._forward_loss_adjoint()
-        self._adam()
 
     def capture(self) -> None:
         """Capture one whole iteration in a CUDA graph.  The capture itself
         does not run the iteration; the warm-up iteration before it does."""
-        self._ensure_workspace()
         s = torch.cuda.Stream()
         s.wait_stream(torch.cuda.current_stream())
         with torch.cuda.stream(s):
@@ -165,18 +143,28 @@ class GGBallIR:
         return self.loss
 
     def step_per_frame(self) -> torch.Tensor:
-        """The same iteration as F plain single-frame launch sequences."""
-        self._ensure_workspace()
+        """The same iteration as F plain single-frame launch sequences (no
+        autograd, no graph), gradients accumulated across frames."""
+        dev = self.canon.device
+        if self._tr1 is None:
+            self._tr1 = torch.empty(1, self.geom.n_sensors, self.geom.n_samples, dtype=torch.float32, device=dev)
+            self._res1 = torch.empty_like(self._tr1)
+        loss = torch.empty(self.F, dtype=torch.float64, device=dev)
         for f in range(self.F):
             tf = self.t[f:f + 1]
-            st = self.state[f:f + 1]
-            deform_balls(self.canon, self.deform[0], self.deform[1], self.deform[2], tf, self.n, out=st)
-            forward(self.geom, st, self.n, out=self.traces[f:f + 1], workspace=self._fws)
-            residual_loss(self.traces[f:f + 1], self.meas[f:f + 1], want_loss=True, want_resid=True,
-                          loss_out=self.loss[f:f + 1], resid_out=self.resid[f:f + 1], workspace=self._lws)
-            self._adjoint_4d(self.resid[f:f + 1], tf, st, None if self.fused else self.g_state[f:f + 1],
-                             accumulate=f > 0)
-        self._adam()
+            forward_4d(self.geom, self.canon, self.deform, tf, self.n, out=self._tr1, plan=self.plan,
+                       workspace=self.bufs.fws)
+            residual_loss(self._tr1, self.meas[f:f + 1], want_loss=True, want_resid=True, loss_out=loss[f:f + 1],
+                          resid_out=self._res1, workspace=self.bufs.lws)
+            if self.fused:
+                adjoint(self.geom, self._res1, canon=self.canon, omega=self.deform[0], theta=self.deform[1],
+                        sigma=self.deform[2], t_frames=tf, n=self.n, accumulate=f > 0,
+                        out=(self.g_canon, self.g_deform[0], self.g_deform[1], self.g_deform[2]))
+            else:
+                adjoint_4d(self.geom, self._res1, self.canon, self.deform, tf, self.n, accumulate=f > 0,
+                           out=(self.g_canon, self.g_deform), plan=self.plan, workspace=self.bufs.aws)
+        self.loss = loss
+        self._adam(self.g_canon, self.g_deform)
         return self.loss
 
     # -- checkpoint / resume -----------------------------------------------------
@@ -200,14 +188,28 @@ class GGBallIR:
         self.step_dev.fill_(self.step_count)
         self.lr_scale = float(sd.get("lr_scale", self.lr_scale))
 
+    def frames_per_chunk(self) -> int:
+        """Frames per launch of the 4D calls (the plan's, else as many as keep
+        one chunk's traces within 32 MiB)."""
+        if self.plan is not None and self.plan.values()["frames_per_chunk"] > 0:
+            return min(self.plan.values()["frames_per_chunk"], self.F)
+        per = self.geom.n_sensors * self.geom.n_samples * 4
+        return max(1, min(self.F, (32 << 20) // per))
+
     def launches_per_step(self, per_frame: bool = False) -> int:
-        from . import forward_plan
-        p = forward_plan(self.geom, self.state[:1] if per_frame else self.state, self.n)
-        fwd = 1 + (1 if p["n_splits"] > 1 else 0)
-        adj = 1 if self.fused else 2  # fused 4D adjoint, or static adjoint + deform backward
-        core = 1 + fwd + 2 + adj  # deform, forward(+split reduce), loss partial+final, adjoint
-        adam = 4  # step counter + three parameter groups
-        return (core * self.F if per_frame else core) + adam
+        """Kernel launches of this library per iteration (memsets excluded)."""
+        from . import forward_plan_for
+        K = 1 if per_frame else self.frames_per_chunk()
+        chunks = self.F if per_frame else -(-self.F // K)
+        tiles = self.plan.values()["tiles"] if self.plan is not None else None
+        p = forward_plan_for(self.geom, self.n, K, tiles)
+        fwd = 2 + (1 if p["n_splits"] > 1 else 0)  # deform, forward (+ split reduce)
+        adj = 1 if self.fused else 3                # fused 4D kernel, or deform + static adjoint + chain rule
+        loss = 2 + 1                                # loss partial + final; residual partial
+        adam = 4                                    # step counter + three parameter groups
+        if self.fused:
+            return chunks * fwd + loss + adj + adam if not per_frame else self.F * (fwd + loss + 1) + adam
+        return chunks * (fwd + adj) + loss + adam if not per_frame else self.F * (fwd + loss + adj) + adam
 
 
 def init_deformation(n_basis: int, stride: int, device, omega_scale: float = 0.0, seed: int = 0) -> torch.Tensor:

@@ -116,3 +116,81 @@ def test_invalid_tile_plans_rejected_on_host(lib):
         assert lib.pa_forward_workspace_size_ex(ctypes.byref(g), ctypes.byref(b), 1, t) == 0, bad
         assert lib.pa_forward_ex(ctypes.byref(g), ctypes.byref(b), 1, None, 0, t, None, 0, None) == \
             _lib.PA_ERR_INVALID_ARG, bad
+
+
+def test_plan_values_round_trip_and_checks_on_host(lib):
+    """pa_plan_from_values / pa_plan_get / pa_plan_destroy need no device; bad
+    values are rejected and leave *out NULL."""
+    from paper_2412_03898_gb300 import _lib
+    h = ctypes.c_void_p()
+    v = (ctypes.c_int32 * 7)(12, 2048, 256, 3, 8, 4, 16)
+    assert lib.pa_plan_from_values(v, ctypes.byref(h)) == _lib.PA_OK and h.value
+    out = (ctypes.c_int32 * 7)()
+    ms = (ctypes.c_float * 2)(9.0, 9.0)
+    assert lib.pa_plan_get(h, out, ms) == _lib.PA_OK
+    assert list(out) == [12, 2048, 256, 3, 8, 4, 16] and list(ms) == [0.0, 0.0]
+    lib.pa_plan_destroy(h)
+    lib.pa_plan_destroy(None)
+    for bad in ((17, 0, 0, 0, 0, 0, 0), (0, 6, 0, 0, 0, 0, 0), (0, 0, 0, 0, 0, -1, 0), (0, 0, 0, 0, 0, 0, 2000)):
+        h = ctypes.c_void_p(1234)
+        assert lib.pa_plan_from_values((ctypes.c_int32 * 7)(*bad), ctypes.byref(h)) == _lib.PA_ERR_INVALID_ARG
+        assert not h.value
+    assert lib.pa_plan_from_values(None, None) == _lib.PA_ERR_INVALID_ARG
+    assert lib.pa_plan_get(None, out, None) == _lib.PA_ERR_INVALID_ARG
+    # the heuristic plan of a valid scene list launches nothing (no device needed)
+    g = _lib.pa_geom(16, 4, 4, 1.5, 40.0, 0.0, 64, 5.0)
+    sc = (_lib.pa_scene * 1)(_lib.pa_scene(g, _lib.pa_balls(16, 10, 12), 1, 16, None, None))
+    h = ctypes.c_void_p()
+    assert lib.pa_plan_create(sc, 1, 0, None, 0, None, ctypes.byref(h)) == _lib.PA_OK and h.value
+    lib.pa_plan_destroy(h)
+    assert lib.pa_plan_create(sc, 0, 0, None, 0, None, ctypes.byref(h)) == _lib.PA_ERR_INVALID_ARG
+    assert lib.pa_plan_create(sc, 1, 1 << 6, None, 0, None, ctypes.byref(h)) == _lib.PA_ERR_INVALID_ARG
+    badg = (_lib.pa_scene * 1)(_lib.pa_scene(_lib.pa_geom(16, 4, 4, 1.5, 40.0, 0.0, 62, 5.0),
+                                             _lib.pa_balls(16, 10, 12), 1, 16, None, None))
+    assert lib.pa_plan_create(badg, 1, 0, None, 0, None, ctypes.byref(h)) == _lib.PA_ERR_INVALID_ARG
+
+
+def test_4d_calls_and_probe_reject_bad_args_on_host(lib):
+    from paper_2412_03898_gb300 import _lib
+    E = _lib.PA_ERR_INVALID_ARG
+    P = ctypes.c_void_p
+    fake = P(256)  # never dereferenced: every call below fails its host-side checks first
+    g = _lib.pa_geom(16, 4, 4, 1.5, 40.0, 0.0, 64, 5.0)
+    good = _lib.pa_canon(16, 16, 16, 16, 4, 4, 3)
+    bad_nb = _lib.pa_canon(16, 16, 16, 16, 4, 4, 0)
+    bad_stride = _lib.pa_canon(16, 16, 16, 16, 6, 6, 3)
+    gr = _lib.pa_grads(16, 16, 16, 16)
+    null_gr = _lib.pa_grads(16, 16, None, 16)
+    assert lib.pa_forward_4d(None, ctypes.byref(good), fake, 2, fake, 0, None, fake, 4096, None) == E
+    assert lib.pa_forward_4d(ctypes.byref(g), ctypes.byref(bad_nb), fake, 2, fake, 0, None, fake, 4096, None) == E
+    assert lib.pa_forward_4d(ctypes.byref(g), ctypes.byref(bad_stride), fake, 2, fake, 0, None, fake, 4096,
+                             None) == E
+    assert lib.pa_forward_4d(ctypes.byref(g), ctypes.byref(good), fake, 2, fake, 1 << 4, None, fake, 4096,
+                             None) == E
+    assert lib.pa_forward_4d(ctypes.byref(g), ctypes.byref(good), fake, 2, P(258), 0, None, fake, 4096, None) == E
+    assert lib.pa_forward_4d(ctypes.byref(g), ctypes.byref(good), None, 2, fake, 0, None, fake, 4096, None) == E
+    assert lib.pa_adjoint_4d(ctypes.byref(g), ctypes.byref(good), fake, 2, fake, None, None, 0, None, fake, 4096,
+                             None) == E
+    assert lib.pa_adjoint_4d(ctypes.byref(g), ctypes.byref(good), fake, 2, fake, None, ctypes.byref(null_gr), 0,
+                             None, fake, 4096, None) == E
+    assert lib.pa_adjoint_4d(ctypes.byref(g), ctypes.byref(good), fake, 2, P(260), None, ctypes.byref(gr), 0,
+                             None, fake, 4096, None) == E
+    assert lib.pa_adjoint_4d(ctypes.byref(g), ctypes.byref(good), fake, 2, fake, None, ctypes.byref(gr), 1 << 3,
+                             None, fake, 4096, None) == E
+    assert lib.pa_forward_4d_workspace_size(ctypes.byref(g), ctypes.byref(bad_nb), 2, None) == 0
+    assert lib.pa_adjoint_4d_workspace_size(None, ctypes.byref(good), 2, None) == 0
+    assert lib.pa_measure_unit_rates(None, None) == E
+
+
+def test_noalloc_loss_rejects_problems_beyond_its_scratch_on_host(lib):
+    """pa_residual_loss_noalloc checks its fixed scratch's capacity on the host
+    before anything else touches the device: 17 frames of 1024 blocks need
+    17408 partials, more than the 16384 it holds.  The pointers are never
+    dereferenced, and this runs where no GPU is visible, so a regression of
+    the check fails the test instead of launching anything."""
+    from paper_2412_03898_gb300 import _lib
+    fake = ctypes.c_void_p(256)
+    assert lib.pa_residual_loss_noalloc(fake, fake, 1024 * 32768, 17, None, fake, None, None) == \
+        _lib.PA_ERR_WORKSPACE
+    # 16384 single-block frames fit; 16385 do not (checked before the device is asked for the scratch)
+    assert lib.pa_residual_loss_noalloc(fake, fake, 4, 16385, None, fake, None, None) == _lib.PA_ERR_WORKSPACE

@@ -141,15 +141,20 @@ def test_autograd_functions(pa):
         assert rel_l2(got[:, ch], g_o[:, ch]) <= GRAD_TOL
 
 
-@pytest.mark.parametrize("keep_states", [True, False])  # static adjoint + chain rule, or the fused 4D adjoint
-def test_autograd_4d(pa, keep_states):
+@pytest.mark.parametrize("fused,frames_per_chunk", [(False, 0), (False, 3), (True, 0)])
+def test_autograd_4d(pa, fused, frames_per_chunk):
+    """PAProject4D (states recomputed per frame chunk in forward and
+    backward, or the fused 4D adjoint kernel) against the oracle's traces and
+    4D gradients, with chunks that divide F unevenly."""
     rng = np.random.default_rng(61)
     n, nb, F = 120, 8, 4
     sc = pa_inputs.small_scene(seed=61, n_balls=n, n_sensors=12, n_samples=512)
     om, th, sg = pa_inputs.random_deform(n, nb, rng)
     t = torch.from_numpy(pa_inputs.frame_times(F)).cuda()
-    params = [dev_pad(x).requires_grad_(True) for x in (sc.balls, om, th, sg)]
-    y = pa.PAProject4D.apply(*params, geometry(sc), t, n, keep_states)
+    canon = dev_pad(sc.balls).requires_grad_(True)
+    deform = torch.stack([dev_pad(x) for x in (om, th, sg)]).requires_grad_(True)
+    plan = pa.Plan.from_values(frames_per_chunk=frames_per_chunk) if frames_per_chunk else None
+    y = pa.PAProject4D.apply(canon, deform, geometry(sc), t, n, plan, None, fused)
     # a random upstream gradient: a constant one makes every true gradient a
     # near-cancelling sum (~1e-6 of its terms), which no FP32 path resolves
     up = rng.standard_normal(tuple(y.shape)).astype(np.float32)
@@ -158,8 +163,8 @@ def test_autograd_4d(pa, keep_states):
     y_o, _ = oracle.forward(st_o, sc.sensors, *_geom_args(sc))
     assert rel_l2(y.detach().cpu().numpy(), y_o) <= TRACE_TOL
     want = oracle.adjoint_4d(sc.balls, om, th, sg, t.cpu().numpy(), sc.sensors, *_geom_args(sc), up)
-    for p, w in zip(params, want):
-        assert rel_l2(p.grad[..., :n].cpu().numpy(), w) <= GRAD_TOL
+    for got, w in zip((canon.grad, deform.grad[0], deform.grad[1], deform.grad[2]), want):
+        assert rel_l2(got[..., :n].cpu().numpy(), w) <= GRAD_TOL
 
 
 @pytest.mark.slow

@@ -90,14 +90,67 @@ def test_adjoint_batched_equals_single_and_oracle(pa):
             assert rel_l2(got[:, ch], want[:, ch]) <= GRAD_TOL
 
 
-def test_tune_batched_accepts_every_default_candidate(pa):
-    from paper_2412_03898_gb300 import autotune
+def test_plan_through_the_c_abi_tunes_and_matches_oracle(pa):
+    """pa_plan_create (timed candidates) called through ctypes, then
+    pa_forward_batched and pa_adjoint_batched with that plan: each scene equals
+    the oracle, and the plan reads back as tuned with legal values."""
+    import ctypes
+    from paper_2412_03898_gb300 import _lib
+    lib = _lib.load()
     scs = _scenes()
-    batch = [pa.Scene(geometry(sc), dev_pad(_states(sc)), sc.n_balls) for sc in scs]
-    best = autotune.tune_batched(batch, reps=1)
-    assert tuple(best) in [tuple(c) for c in autotune.DEFAULT_CANDIDATES]
-    pa.forward_batched(batch, tiles=best)
+    rng = np.random.default_rng(9)
+    batch = []
+    for sc in scs:
+        st = dev_pad(_states(sc))
+        b = pa.Scene(geometry(sc), st, sc.n_balls)
+        b.traces = torch.empty(b.F, sc.n_sensors, sc.n_samples, device="cuda")
+        b.trace_grad = torch.from_numpy(
+            rng.standard_normal((b.F, sc.n_sensors, sc.n_samples)).astype(np.float32)).cuda()
+        b.grad_state = torch.empty_like(st)
+        batch.append(b)
+    arr = (_lib.pa_scene * len(batch))(*[b.struct() for b in batch])
+    need = lib.pa_plan_workspace_size(arr, len(batch))
+    ws = torch.empty(max(need, 256), dtype=torch.uint8, device="cuda")
+    stream = ctypes.c_void_p(torch.cuda.current_stream().cuda_stream)
+    h = ctypes.c_void_p()
+    assert lib.pa_plan_create(arr, len(batch), _lib.PA_PLAN_TUNE, ws.data_ptr(), ws.numel(), stream,
+                              ctypes.byref(h)) == 0
+    vals = (ctypes.c_int32 * 7)()
+    ms = (ctypes.c_float * 2)()
+    assert lib.pa_plan_get(h, vals, ms) == 0
+    assert 1 <= vals[0] <= 16 and vals[1] % 4 == 0 and vals[4] in (1, 2, 4, 8, 16) and vals[6] in (4, 8, 16, 32)
+    assert ms[0] > 0 and ms[1] > 0
+    for b in batch:
+        b.traces.fill_(3.0)
+    assert lib.pa_forward_batched(arr, len(batch), 0, h, ws.data_ptr(), ws.numel(), stream) == 0
+    assert lib.pa_adjoint_batched(arr, len(batch), 0, h, ws.data_ptr(), ws.numel(), stream) == 0
     pa.device_error()
+    lib.pa_plan_destroy(h)
     for sc, b in zip(scs, batch):
         y_o, _ = oracle.forward(_states(sc), sc.sensors, sc.c, sc.fs, sc.t0, sc.n_samples, sc.kappa)
         assert rel_l2(b.traces.cpu().numpy(), y_o) <= TRACE_TOL
+        want = oracle.adjoint_state(_states(sc), sc.sensors, sc.c, sc.fs, sc.t0, sc.n_samples, sc.kappa,
+                                    b.trace_grad.cpu().numpy())
+        got = b.grad_state[..., :sc.n_balls].cpu().numpy()
+        for ch in range(5):
+            assert rel_l2(got[:, ch], want[:, ch]) <= GRAD_TOL
+
+
+def test_single_scene_plan_and_autotune_cache(pa, tmp_path, monkeypatch):
+    """A one-scene tuned plan (ball splits by the planner) drives pa_forward_ex
+    to the oracle's traces; the autotuner's file cache round-trips it."""
+    from paper_2412_03898_gb300 import autotune
+    monkeypatch.setenv("PA_TILE_CACHE", str(tmp_path / "tiles.json"))
+    monkeypatch.setattr(autotune, "_cache", {})
+    sc = _scenes()[2]
+    st = dev_pad(_states(sc))
+    geom = geometry(sc)
+    plan = autotune.tune_forward_plan(geom, st, sc.n_balls)
+    v = plan.values()
+    assert v["tuned"] and v["forward_ms"] > 0
+    y = pa.forward(geom, st, sc.n_balls, tiles=v["tiles"])
+    y_o, _ = oracle.forward(_states(sc), sc.sensors, sc.c, sc.fs, sc.t0, sc.n_samples, sc.kappa)
+    assert rel_l2(y.cpu().numpy(), y_o) <= TRACE_TOL
+    monkeypatch.setattr(autotune, "_cache", {})
+    again = autotune.tune_forward_plan(geom, st, sc.n_balls)  # from the file, not re-timed
+    assert again.values()["tiles"] == v["tiles"] and not again.values()["tuned"]

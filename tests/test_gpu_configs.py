@@ -85,10 +85,10 @@ def test_batched_16_sampled(pa):
         st = dev_pad(sc.frames if sc.frames is not None else sc.balls[None])
         b = pa.Scene(geometry(sc), st, sc.n_balls)
         scenes.append(b)
-    tiles = tune_batched(scenes)
+    plan = tune_batched(scenes)
     for b in scenes:
         b.traces = None
-    pa.forward_batched(scenes, tiles=tiles)
+    pa.forward_batched(scenes, plan=plan)
     for b in scenes:
         b.trace_grad = torch.randn_like(b.traces)
     pa.adjoint_batched(scenes)

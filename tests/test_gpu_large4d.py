@@ -1,6 +1,7 @@
 """Full-size 4D workload (1,000,000 balls in a 60 mm vessel tree, 1024 sensors
 on an 80 mm hemisphere, 4096 samples, 50 frames, Nb = 65) in the launch
-configuration the library uses for it (all frames per launch), checked on
+configuration the IR uses for it (pa_forward_4d / pa_adjoint_4d, states
+recomputed per frame chunk), and through the fused 4D adjoint, checked on
 sampled outputs the FP64 oracle can compute one by one: traces of 8 random
 sensors at the first and last frame, and the 4D gradients of 32 random balls
 for a residual that is non-zero on those two frames (the oracle sums its
@@ -24,10 +25,11 @@ def test_large_4d_sampled_parity():
     om, th, sg = pa_inputs.random_deform(n, nb, rng, omega_scale=0.02)
     t = pa_inputs.frame_times(F)
     geom = geometry(sc)
-    canon, omega, theta, sigma = (dev_pad(x) for x in (sc.balls, om, th, sg))
+    canon = dev_pad(sc.balls)
+    deform = torch.stack([dev_pad(x) for x in (om, th, sg)])
+    omega, theta, sigma = deform[0], deform[1], deform[2]
     t_dev = torch.from_numpy(t).cuda()
-    state = pa.deform_balls(canon, omega, theta, sigma, t_dev, n)
-    traces = pa.forward(geom, state, n)
+    traces = pa.forward_4d(geom, canon, deform, t_dev, n)
     pa.device_error()
     frames = [0, F - 1]
     pick_s = np.sort(rng.choice(sc.n_sensors, 8, replace=False))
@@ -36,22 +38,24 @@ def test_large_4d_sampled_parity():
         y_o, _ = oracle.forward(st_o, sc.sensors[:, pick_s], sc.c, sc.fs, sc.t0, sc.n_samples, sc.kappa)
         got = traces[f, pick_s].cpu().numpy()
         assert rel_l2(got, y_o[0]) <= TRACE_TOL, f
-    del state, traces
+    del traces
 
     g = torch.zeros(F, sc.n_sensors, sc.n_samples, device="cuda")
     g_host = {f: rng.standard_normal((1, sc.n_sensors, sc.n_samples)).astype(np.float32) for f in frames}
     for f in frames:
         g[f] = torch.from_numpy(g_host[f][0]).cuda()
-    gc, go, gt, gs = pa.adjoint(geom, g, canon=canon, omega=omega, theta=theta, sigma=sigma, t_frames=t_dev, n=n)
-    pa.device_error()
     pick = np.sort(rng.choice(n, 32, replace=False))
     want = None
     for f in frames:
         w = oracle.adjoint_4d(sc.balls[:, pick], om[:, :, pick], th[:, :, pick], sg[:, :, pick], t[f:f + 1],
                               sc.sensors, sc.c, sc.fs, sc.t0, sc.n_samples, sc.kappa, g_host[f])
         want = w if want is None else tuple(a + b for a, b in zip(want, w))
-    for got, w, name in ((gc, want[0], "canon"), (go, want[1], "omega"), (gt, want[2], "theta"),
-                         (gs, want[3], "sigma")):
-        arr = got[..., pick].cpu().numpy()
-        for ch in range(5):
-            assert rel_l2(arr[ch], w[ch]) <= GRAD_TOL, (name, ch)
+    gc, gd = pa.adjoint_4d(geom, g, canon, deform, t_dev, n)
+    pa.device_error()
+    fused = pa.adjoint(geom, g, canon=canon, omega=omega, theta=theta, sigma=sigma, t_frames=t_dev, n=n)
+    pa.device_error()
+    for form, grads in (("recompute", (gc, gd[0], gd[1], gd[2])), ("fused", fused)):
+        for got, w, name in zip(grads, want, ("canon", "omega", "theta", "sigma")):
+            arr = got[..., pick].cpu().numpy()
+            for ch in range(5):
+                assert rel_l2(arr[ch], w[ch]) <= GRAD_TOL, (form, name, ch)
