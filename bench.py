@@ -109,6 +109,8 @@ def parse():
     ap.add_argument("--steps-batched", type=int, default=2)
     ap.add_argument("--no-autotune", action="store_true")
     ap.add_argument("--no-imaging", action="store_true", help="skip the UBP / splat / MAP / SSIM leg")
+    ap.add_argument("--no-static", action="store_true",
+                    help="skip the static-100k headline step (prints the other legs only; for profiling a leg)")
     ap.add_argument("--no-large4d", action="store_true",
                     help="skip the 1M-ball, 50-frame IR iterations (4d-1m-50f; batched graph vs per-frame)")
     ap.add_argument("--heart-ir", type=int, default=0, metavar="ITERS",
@@ -295,6 +297,24 @@ CONFIG_DESC = ("static-100k: 100,000-ball synthetic vessel tree (20 branching tu
 # ---------------------------------------------------------------------------
 # our arm
 # ---------------------------------------------------------------------------
+def run_legs(args, pa, pa_inputs, dev, flush) -> dict:
+    """The legs beside the headline (each skipped by its --no-* switch)."""
+    out = {}
+    if not args.no_4d:
+        out["ir4d"] = bench_4d(args, pa, pa_inputs, dev, flush)
+    if not args.no_batched:
+        out["batched"] = bench_batched(args, pa, pa_inputs, dev, flush)
+    if not args.no_imaging:
+        out["imaging"] = bench_imaging(args, pa, pa_inputs, dev, flush)
+    if args.ir_quality_iters > 0 and not args.no_4d:
+        out["ir_quality"] = bench_ir_quality(args, pa, pa_inputs, dev)
+    if not args.no_large4d:
+        out["large4d"] = bench_large4d(args, pa, pa_inputs, dev)
+    if args.heart_ir > 0:
+        out["heart_ir"] = bench_heart_ir(args, pa, pa_inputs, dev)
+    return out
+
+
 def run_ours(args):
     import torch
     world, rank, local = dist_setup(args)
@@ -302,6 +322,13 @@ def run_ours(args):
     dev = torch.device("cuda", local)
     import pa_inputs
     import paper_2412_03898_gb300 as pa
+
+    if args.no_static:
+        flush = torch.empty(512 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)
+        legs = run_legs(args, pa, pa_inputs, dev, flush)
+        if rank == 0:
+            print(json.dumps({"metric": METRIC, "note": "legs only (--no-static): no headline value", **legs}))
+        return 0
 
     sc = pa_inputs.config_scene(2)
     n = sc.n_balls
@@ -398,20 +425,7 @@ def run_ours(args):
     e2e_ms = max_over_ranks(e2e_ms, world, dev)
     pa.device_error()
 
-    ir4d = None
-    if not args.no_4d:
-        ir4d = bench_4d(args, pa, pa_inputs, dev, flush)
-    batched = None
-    if not args.no_batched:
-        batched = bench_batched(args, pa, pa_inputs, dev, flush)
-    imaging = None
-    if not args.no_imaging:
-        imaging = bench_imaging(args, pa, pa_inputs, dev, flush)
-    ir_quality = None
-    if args.ir_quality_iters > 0 and not args.no_4d:
-        ir_quality = bench_ir_quality(args, pa, pa_inputs, dev)
-    large4d = None if args.no_large4d else bench_large4d(args, pa, pa_inputs, dev)
-    heart_ir = bench_heart_ir(args, pa, pa_inputs, dev) if args.heart_ir > 0 else None
+    legs = run_legs(args, pa, pa_inputs, dev, flush)
     clocks = sampler.stop()
 
     fwd_avg = statistics.mean(t_fwd)
@@ -450,18 +464,7 @@ def run_ours(args):
         "kernels_ms": {"forward": fwd_avg, "loss": statistics.mean(t_loss), "adjoint": adj_avg},
         "fwd_contrib_per_s": C / (fwd_avg * 1e-3), "adj_contrib_per_s": C / (adj_avg * 1e-3),
     }
-    if ir4d is not None:
-        line["ir4d"] = ir4d
-    if batched is not None:
-        line["batched"] = batched
-    if imaging is not None:
-        line["imaging"] = imaging
-    if ir_quality is not None:
-        line["ir_quality"] = ir_quality
-    if large4d is not None:
-        line["large4d"] = large4d
-    if heart_ir is not None:
-        line["heart_ir"] = heart_ir
+    line.update(legs)
     if rank == 0 and world == 1 and not args.no_cpu:
         line["cpu_baseline"] = cpu_baseline(sc)
         line["cpu_baseline_single_core"] = cpu_baseline_single_core(sc)
@@ -515,6 +518,7 @@ def bench_4d(args, pa, pa_inputs, dev, flush):
         out[f"{mode}_loss"] = float(ir.loss.sum().item())
         del ir
     out["speedup_batched_vs_per_frame"] = res["batched_graph"] / res["per_frame"]
+    out["frames_per_launch"] = GGBallIR(geom, canon, deform, t, meas, n).frames_per_chunk()
     out["contrib_per_s_batched"] = C * res["batched_graph"]
     out["contrib_per_s_per_frame"] = C * res["per_frame"]
     return out
@@ -680,14 +684,16 @@ def bench_large4d(args, pa, pa_inputs, dev):
     ir.step_per_frame()
     s_pf = timed(ir.step_per_frame, 1)
     pa.device_error()
+    out["frames_per_launch"] = ir.frames_per_chunk()
     out.update({"iters_per_s": 1.0 / s_graph, "seconds_per_iteration": s_graph,
                 "per_frame_iters_per_s": 1.0 / s_pf, "per_frame_seconds_per_iteration": s_pf,
                 "speedup_batched_vs_per_frame": s_pf / s_graph,
                 "contrib_per_s": C / s_graph, "per_frame_contrib_per_s": C / s_pf,
                 "iterations_timed": {"batched_graph": 2, "per_frame": 1},
                 "device_memory_gb": (torch.cuda.max_memory_allocated(dev) - base) / 1e9,
-                "device_memory_note": "peak bytes allocated by the IR (parameters, Adam moments, gradients, "
-                                      "per-frame buffers, workspaces) beyond the measurements"})
+                "device_memory_note": "peak bytes allocated by the IR beyond the measurements: parameters, Adam "
+                                      "moments, gradients, traces, residual and one frame chunk of states; no "
+                                      "[F][5][N] buffer"})
     return out
 
 

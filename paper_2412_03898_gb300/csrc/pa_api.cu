@@ -113,34 +113,66 @@ pa::Acq make_acq(const pa_geom *g) {
 
 inline int cuda_status(cudaError_t e) { return e == cudaSuccess ? PA_OK : PA_ERR_CUDA; }
 
-// Launches the forward over F frames of states [F][5][stride] with the plan
-// for (tiles, F); arguments already checked.
+// The forward's split partials ([splits][frames][S][T] floats) are kept
+// within kMaxPartialBytes by launching frames in chunks: the chunk is halved
+// from all frames until its plan's partials fit.
+constexpr size_t kMaxPartialBytes = 1ull << 30;
+
+struct FwdChunking {
+  int frames;  // frames per launch
+  size_t ws;   // workspace bytes of the largest chunk
+};
+
+pa::FwdPlan plan_for(const DevInfo *d, const pa_geom *g, long long n, int F, const int32_t *tiles) {
+  return pa::forward_plan(g->n_sensors, g->n_samples, n, F, d->sms, tiles ? tiles[0] : 0, tiles ? tiles[1] : 0,
+                          tiles ? tiles[2] : 0, tiles ? tiles[3] : 0, tiles ? tiles[4] : 0);
+}
+
+FwdChunking forward_chunking(const DevInfo *d, const pa_geom *g, long long n, int F, const int32_t *tiles) {
+  FwdChunking c{std::max(F, 1), 0};
+  c.ws = plan_for(d, g, n, c.frames, tiles).ws_bytes;
+  while (c.ws > kMaxPartialBytes && c.frames > 1) {
+    c.frames = std::max(1, c.frames / 2);
+    c.ws = plan_for(d, g, n, c.frames, tiles).ws_bytes;
+  }
+  if (F > c.frames && F % c.frames != 0) c.ws = std::max(c.ws, plan_for(d, g, n, F % c.frames, tiles).ws_bytes);
+  return c;
+}
+
+// Launches the forward over F frames of states [F][5][stride] (in frame
+// chunks that keep the split partials within kMaxPartialBytes); arguments
+// already checked.
 int forward_launch(const DevInfo *d, const pa_geom *geom, const float *state, long long n, long long stride,
                    int32_t F, float *traces, uint32_t flags, const int32_t *tiles, void *ws, size_t ws_bytes,
                    cudaStream_t st) {
-  const pa::FwdPlan p = pa::forward_plan(geom->n_sensors, geom->n_samples, n, F, d->sms, tiles ? tiles[0] : 0,
-                                         tiles ? tiles[1] : 0, tiles ? tiles[2] : 0, tiles ? tiles[3] : 0,
-                                         tiles ? tiles[4] : 0);
-  if (p.smem > (size_t)d->max_smem) return PA_ERR_INVALID_ARG;
-  if (p.ws_bytes > 0 && (ws == nullptr || ws_bytes < p.ws_bytes || !aligned(ws, 256))) return PA_ERR_WORKSPACE;
-  pa::FwdArgs a;
-  a.q = make_acq(geom);
-  a.state = state;
-  a.n = n;
-  a.stride = stride;
-  a.F = F;
-  a.out = traces;
-  a.partial = static_cast<float *>(ws);
-  a.s_tile = p.s_tile;
-  a.t_tile = p.t_tile;
-  a.nb_tile = p.nb_tile;
-  a.n_splits = p.n_splits;
-  a.n_stiles = p.n_stiles;
-  a.n_ttiles = p.n_ttiles;
-  a.balls_per_split = p.balls_per_split;
-  a.flags = flags;
-  a.err = d->err;
-  return cuda_status(pa::launch_forward(a, p, (flags & PA_PROFILE_UNIFORM) != 0, st));
+  const FwdChunking ch = forward_chunking(d, geom, n, F, tiles);
+  if (ch.ws > 0 && (ws == nullptr || ws_bytes < ch.ws || !aligned(ws, 256))) return PA_ERR_WORKSPACE;
+  const size_t per_frame = (size_t)geom->n_sensors * geom->n_samples;
+  for (int f0 = 0; f0 < F; f0 += ch.frames) {
+    const int k = std::min(ch.frames, F - f0);
+    const pa::FwdPlan p = plan_for(d, geom, n, k, tiles);
+    if (p.smem > (size_t)d->max_smem) return PA_ERR_INVALID_ARG;
+    pa::FwdArgs a;
+    a.q = make_acq(geom);
+    a.state = state + (size_t)f0 * 5 * stride;
+    a.n = n;
+    a.stride = stride;
+    a.F = k;
+    a.out = traces + per_frame * f0;
+    a.partial = static_cast<float *>(ws);
+    a.s_tile = p.s_tile;
+    a.t_tile = p.t_tile;
+    a.nb_tile = p.nb_tile;
+    a.n_splits = p.n_splits;
+    a.n_stiles = p.n_stiles;
+    a.n_ttiles = p.n_ttiles;
+    a.balls_per_split = p.balls_per_split;
+    a.flags = flags;
+    a.err = d->err;
+    const int rc = cuda_status(pa::launch_forward(a, p, (flags & PA_PROFILE_UNIFORM) != 0, st));
+    if (rc) return rc;
+  }
+  return PA_OK;
 }
 
 int forward_impl(const pa_geom *geom, const pa_balls *balls, int32_t F, float *traces, uint32_t flags,
@@ -163,14 +195,16 @@ int forward_impl(const pa_geom *geom, const pa_balls *balls, int32_t F, float *t
   return forward_launch(d, geom, balls->state, balls->n, balls->stride, F, traces, flags, tiles, ws, ws_bytes, st);
 }
 
-// Frames per launch of the 4D calls: as many as keep one launch's traces (or
-// residuals) within 32 MiB, so that they stay in L2 between the kernels of a
-// chunk, at least 1 and at most F; a plan may fix the number.
-int frames_per_chunk(const pa_plan *plan, int S, int T, int F) {
+// Frames per launch of the 4D calls: as many as keep one chunk's states and
+// state gradients ([K][5][stride] each) within kChunkBudget, at least 1 and
+// at most F; a plan may fix the number.  The budget bounds the 4D calls'
+// memory whatever the number of frames.
+constexpr long long kChunkBudget = 64LL << 20;
+int frames_per_chunk(const pa_plan *plan, long long stride, int F) {
   if (F <= 0) return 1;
   if (plan && plan->frames_per_chunk > 0) return std::min(plan->frames_per_chunk, F);
-  const long long per = std::max(1LL, (long long)S * T * (long long)sizeof(float));
-  return (int)std::max(1LL, std::min<long long>((32LL << 20) / per, F));
+  const long long per = std::max(1LL, 2LL * 5 * (long long)sizeof(float) * stride);
+  return (int)std::max(1LL, std::min<long long>(kChunkBudget / per, F));
 }
 
 inline size_t round256(size_t b) { return (b + 255) & ~(size_t)255; }
@@ -184,13 +218,8 @@ inline size_t chunk_state_bytes(const pa_canon *c, int K) {
 size_t forward_4d_partials(const DevInfo *d, const pa_geom *g, const pa_canon *c, int32_t F, int K,
                            const int32_t *tiles) {
   size_t ws = 0;
-  for (int k : {K, F % K}) {
-    if (k <= 0) continue;
-    const pa::FwdPlan p = pa::forward_plan(g->n_sensors, g->n_samples, c->n, k, d->sms, tiles ? tiles[0] : 0,
-                                           tiles ? tiles[1] : 0, tiles ? tiles[2] : 0, tiles ? tiles[3] : 0,
-                                           tiles ? tiles[4] : 0);
-    ws = std::max(ws, p.ws_bytes);
-  }
+  for (int k : {K, F % K})
+    if (k > 0) ws = std::max(ws, forward_chunking(d, g, c->n, k, tiles).ws);
   return ws;
 }
 
@@ -310,10 +339,7 @@ size_t pa_forward_workspace_size_ex(const pa_geom *geom, const pa_balls *balls, 
   if (!tiles_ok(tiles) || check_geom(geom) || check_balls(balls) || n_frames <= 0 || balls->n == 0) return 0;
   const DevInfo *d = dev_info();
   if (!d) return 0;
-  const pa::FwdPlan p = pa::forward_plan(geom->n_sensors, geom->n_samples, balls->n, n_frames, d->sms,
-                                         tiles ? tiles[0] : 0, tiles ? tiles[1] : 0, tiles ? tiles[2] : 0,
-                                         tiles ? tiles[3] : 0, tiles ? tiles[4] : 0);
-  return p.ws_bytes;
+  return forward_chunking(d, geom, balls->n, n_frames, tiles).ws;
 }
 
 size_t pa_forward_workspace_size(const pa_geom *geom, const pa_balls *balls, int32_t n_frames) {
@@ -758,9 +784,8 @@ size_t pa_plan_workspace_size(const pa_scene *scenes, int32_t n_scenes) {
   if (sc.n_frames <= 0 || sc.balls.n == 0) return ws;
   for (int c = -1; c < kNumTileCandidates; ++c) {
     const int32_t *t = c < 0 ? nullptr : kTileCandidates[c];
-    const pa::FwdPlan p = pa::forward_plan(sc.geom.n_sensors, sc.geom.n_samples, sc.balls.n, sc.n_frames, d->sms,
-                                           t ? t[0] : 0, t ? t[1] : 0, t ? t[2] : 0, t ? t[3] : 0, t ? t[4] : 0);
-    if (p.smem <= (size_t)d->max_smem) ws = std::max(ws, p.ws_bytes);
+    const pa::FwdPlan p = plan_for(d, &sc.geom, sc.balls.n, 1, t);
+    if (p.smem <= (size_t)d->max_smem) ws = std::max(ws, forward_chunking(d, &sc.geom, sc.balls.n, sc.n_frames, t).ws);
   }
   return ws;
 }
@@ -908,7 +933,7 @@ size_t pa_forward_4d_workspace_size(const pa_geom *geom, const pa_canon *canon, 
   if (!tiles_ok(tiles)) return 0;
   const DevInfo *d = dev_info();
   if (!d) return 0;
-  const int K = frames_per_chunk(plan, geom->n_sensors, geom->n_samples, n_frames);
+  const int K = frames_per_chunk(plan, canon->stride, n_frames);
   return chunk_state_bytes(canon, K) + forward_4d_partials(d, geom, canon, n_frames, K, tiles);
 }
 
@@ -932,7 +957,7 @@ int32_t pa_forward_4d(const pa_geom *geom, const pa_canon *canon, const float *t
     if (flags & PA_ACCUMULATE) return PA_OK;
     return cuda_status(cudaMemsetAsync(traces, 0, sizeof(float) * per_frame * n_frames, st));
   }
-  const int K = frames_per_chunk(plan, geom->n_sensors, geom->n_samples, n_frames);
+  const int K = frames_per_chunk(plan, canon->stride, n_frames);
   const size_t sbytes = chunk_state_bytes(canon, K);
   const size_t need = sbytes + forward_4d_partials(d, geom, canon, n_frames, K, tiles);
   if (workspace == nullptr || workspace_bytes < need || !aligned(workspace, 256)) return PA_ERR_WORKSPACE;
@@ -953,7 +978,7 @@ int32_t pa_forward_4d(const pa_geom *geom, const pa_canon *canon, const float *t
 size_t pa_adjoint_4d_workspace_size(const pa_geom *geom, const pa_canon *canon, int32_t n_frames,
                                     const pa_plan *plan) {
   if (check_geom(geom) || check_canon(canon) || n_frames <= 0 || canon->n == 0) return 0;
-  const int K = frames_per_chunk(plan, geom->n_sensors, geom->n_samples, n_frames);
+  const int K = frames_per_chunk(plan, canon->stride, n_frames);
   return 2 * chunk_state_bytes(canon, K);
 }
 
@@ -982,7 +1007,7 @@ int32_t pa_adjoint_4d(const pa_geom *geom, const pa_canon *canon, const float *t
     if (e == cudaSuccess) e = cudaMemsetAsync(grads->sigma, 0, rows * 5 * canon->n_basis, st);
     return cuda_status(e);
   }
-  const int K = frames_per_chunk(plan, geom->n_sensors, geom->n_samples, n_frames);
+  const int K = frames_per_chunk(plan, canon->stride, n_frames);
   const size_t sbytes = chunk_state_bytes(canon, K);
   if (workspace == nullptr || workspace_bytes < 2 * sbytes || !aligned(workspace, 256)) return PA_ERR_WORKSPACE;
   float *states = static_cast<float *>(workspace);

@@ -33,12 +33,21 @@ def test_large_4d_sampled_parity():
     pa.device_error()
     frames = [0, F - 1]
     pick_s = np.sort(rng.choice(sc.n_sensors, 8, replace=False))
+    # pa_forward over all 50 frames' stored states: split partials bounded at
+    # 1 GiB by frame chunks inside the call
+    state = pa.deform_balls(canon, omega, theta, sigma, t_dev, n)
+    ws_bytes = pa.forward_workspace_size(geom, state, n)
+    assert 0 < ws_bytes <= 1 << 30
+    traces_all = pa.forward(geom, state, n)
+    pa.device_error()
+    del state
     for f in frames:
         st_o = oracle.deform(sc.balls, om, th, sg, t[f:f + 1])
         y_o, _ = oracle.forward(st_o, sc.sensors[:, pick_s], sc.c, sc.fs, sc.t0, sc.n_samples, sc.kappa)
-        got = traces[f, pick_s].cpu().numpy()
-        assert rel_l2(got, y_o[0]) <= TRACE_TOL, f
-    del traces
+        for form, tr in (("forward_4d", traces), ("forward", traces_all)):
+            got = tr[f, pick_s].cpu().numpy()
+            assert rel_l2(got, y_o[0]) <= TRACE_TOL, (form, f)
+    del traces, traces_all
 
     g = torch.zeros(F, sc.n_sensors, sc.n_samples, device="cuda")
     g_host = {f: rng.standard_normal((1, sc.n_sensors, sc.n_samples)).astype(np.float32) for f in frames}
