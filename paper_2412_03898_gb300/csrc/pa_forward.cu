@@ -232,37 +232,74 @@ __device__ __forceinline__ bool forward_item(const Acq &q, const float *state_f,
         const bool valid = w.W > 0;
         const int nv = __popc(__ballot_sync(FULL, valid));
         if (nv == 0) continue;
-        // sort by first sample; invalid pairs last; lane index in the low bits
-        const unsigned key = warp_sort(((valid ? (unsigned)(w.klo - k0) : 0xffffu) << 5) | (unsigned)lane, lane);
-        // lane i takes the i-th pair in that order (positions >= nv are pads)
-        const int src = (int)(key & 31u);
-        const float pu0 = __shfl_sync(FULL, w.u0, src);
-        const float pdu = __shfl_sync(FULL, w.du, src);
-        const float pamp = __shfl_sync(FULL, w.amp, src);
-        const int pW = __shfl_sync(FULL, w.W, src);
-        const bool real = lane < nv;
-        const int kl = (int)(key >> 5);  // first sample relative to k0
-        // the group's first sample (sorted: its first member's) and last sample
-        const int kmin = __shfl_sync(FULL, kl, lane & ~(G - 1));
-        int kmax = real ? kl + pW - 1 : -1;
-#pragma unroll
-        for (int o = 1; o < G; o <<= 1) kmax = max(kmax, __shfl_xor_sync(FULL, kmax, o));
-        const int nsteps = ((kmax - kmin) >> 5) + 1;
-        // phase at the group's first sample: kmin - kl is a small exact
-        // integer; pads sit far outside every window with zero amplitude
-        const float us = real ? fmaf((float)(kmin - kl), -pdu, pu0) : 1e30f;
-        const float nd = real ? -pdu : 0.f;
-        const float am = real ? pamp : 0.f;
-        __syncwarp();  // the previous chunk's groups are done with the records
-        if (G == 1) {
-          reinterpret_cast<float4 *>(mygrp)[lane] = make_float4(us, nd, am, __int_as_float(kmin | (nsteps << 16)));
-        } else {
-          const int j = lane & (G - 1);
-          float *r = mygrp + (lane / G) * GS;
+        if constexpr (G == 16) {
+          // Two groups of 16 per chunk: a pivot at the mean first sample splits
+          // the pairs (below it first, then the other valid pairs, then the
+          // invalid ones as zero-amplitude pads).  The order inside a group
+          // does not matter, since each group is swept over the union of its
+          // windows, so this ballot partition replaces a full sort.
+          const unsigned vmask = __ballot_sync(FULL, valid);
+          const int key = valid ? w.klo - k0 : 0;  // first sample relative to k0
+          const int sum = (int)__reduce_add_sync(FULL, (unsigned)key);
+          const bool below = valid && key * nv < sum;
+          const unsigned bmask = __ballot_sync(FULL, below);
+          const unsigned lt = (1u << lane) - 1u;
+          const int nb = __popc(bmask);
+          const int pos = below ? __popc(bmask & lt)
+                                : (valid ? nb + __popc(vmask & ~bmask & lt) : nv + __popc(~vmask & lt));
+          const bool first = pos < 16;
+          const int kend = valid ? key + w.W - 1 : -1;
+          const int kmin0 = __reduce_min_sync(FULL, valid && first ? key : 0x7fffffff);
+          const int kmin1 = __reduce_min_sync(FULL, valid && !first ? key : 0x7fffffff);
+          const int kmax0 = __reduce_max_sync(FULL, first ? kend : -1);
+          const int kmax1 = __reduce_max_sync(FULL, first ? -1 : kend);
+          const int kmin = first ? kmin0 : kmin1;
+          const int nsteps = (((first ? kmax0 : kmax1) - kmin) >> 5) + 1;
+          // phase at the group's first sample (kmin - key is a small exact
+          // integer); pads sit far outside every window with zero amplitude
+          const float us = valid ? fmaf((float)(kmin - key), -w.du, w.u0) : 1e30f;
+          const float nd = valid ? -w.du : 0.f;
+          const float am = valid ? w.amp : 0.f;
+          __syncwarp();  // the previous chunk's groups are done with the records
+          const int j = pos & 15;
+          float *r = mygrp + (pos >> 4) * GS;
           r[(j >> 1) * 4 + (j & 1)] = us;
           r[(j >> 1) * 4 + 2 + (j & 1)] = nd;
           r[4 * H + j] = am;
           if (j == 0) reinterpret_cast<int2 *>(r + 6 * H)[0] = make_int2(kmin, nsteps);
+        } else {
+          // sort by first sample; invalid pairs last; lane index in the low bits
+          const unsigned key = warp_sort(((valid ? (unsigned)(w.klo - k0) : 0xffffu) << 5) | (unsigned)lane, lane);
+          // lane i takes the i-th pair in that order (positions >= nv are pads)
+          const int src = (int)(key & 31u);
+          const float pu0 = __shfl_sync(FULL, w.u0, src);
+          const float pdu = __shfl_sync(FULL, w.du, src);
+          const float pamp = __shfl_sync(FULL, w.amp, src);
+          const int pW = __shfl_sync(FULL, w.W, src);
+          const bool real = lane < nv;
+          const int kl = (int)(key >> 5);  // first sample relative to k0
+          // the group's first sample (sorted: its first member's) and last sample
+          const int kmin = __shfl_sync(FULL, kl, lane & ~(G - 1));
+          int kmax = real ? kl + pW - 1 : -1;
+#pragma unroll
+          for (int o = 1; o < G; o <<= 1) kmax = max(kmax, __shfl_xor_sync(FULL, kmax, o));
+          const int nsteps = ((kmax - kmin) >> 5) + 1;
+          // phase at the group's first sample: kmin - kl is a small exact
+          // integer; pads sit far outside every window with zero amplitude
+          const float us = real ? fmaf((float)(kmin - kl), -pdu, pu0) : 1e30f;
+          const float nd = real ? -pdu : 0.f;
+          const float am = real ? pamp : 0.f;
+          __syncwarp();  // the previous chunk's groups are done with the records
+          if (G == 1) {
+            reinterpret_cast<float4 *>(mygrp)[lane] = make_float4(us, nd, am, __int_as_float(kmin | (nsteps << 16)));
+          } else {
+            const int j = lane & (G - 1);
+            float *r = mygrp + (lane / G) * GS;
+            r[(j >> 1) * 4 + (j & 1)] = us;
+            r[(j >> 1) * 4 + 2 + (j & 1)] = nd;
+            r[4 * H + j] = am;
+            if (j == 0) reinterpret_cast<int2 *>(r + 6 * H)[0] = make_int2(kmin, nsteps);
+          }
         }
         __syncwarp();
         const float lf = (float)lane;
