@@ -311,11 +311,12 @@ PA_API size_t pa_forward_4d_workspace_size(const pa_geom *geom, const pa_canon *
 
 /* Forward projection of a 4D sequence straight from the GGBall parameters
  * (Eq. 1-2, Sec. 2.2; radiator as pa_forward): frames are processed in
- * chunks of K (the plan's frames per launch, else as many as keep one
- * chunk's traces within 32 MiB of L2), each chunk deformed into the
- * workspace and projected in one launch, so the states of at most K frames
- * exist at any time: memory is the canonical cloud, its deformation
- * parameters and one chunk, whatever n_frames is.
+ * chunks of K (the plan's frames per launch, else K = floor(3 n_basis / 16),
+ * which keeps a chunk's states and state gradients within an eighth of the
+ * deformation parameters' memory), each chunk deformed into the workspace
+ * and projected, so the states of at most K frames exist at any time:
+ * memory is the canonical cloud, its deformation parameters and one chunk,
+ * whatever n_frames is.
  *   t_frames  device [n_frames] normalised frame times
  *   traces    device [n_frames][n_sensors][n_samples], 16-byte aligned
  *   workspace device, 256-byte aligned, pa_forward_4d_workspace_size() bytes

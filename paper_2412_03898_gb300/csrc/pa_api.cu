@@ -196,15 +196,16 @@ int forward_impl(const pa_geom *geom, const pa_balls *balls, int32_t F, float *t
 }
 
 // Frames per launch of the 4D calls: as many as keep one chunk's states and
-// state gradients ([K][5][stride] each) within kChunkBudget, at least 1 and
-// at most F; a plan may fix the number.  The budget bounds the 4D calls'
-// memory whatever the number of frames.
-constexpr long long kChunkBudget = 64LL << 20;
-int frames_per_chunk(const pa_plan *plan, long long stride, int F) {
+// state gradients ([K][5][stride] floats each, 40 B per ball and frame)
+// within an eighth of the deformation parameters' own memory ((omega, theta,
+// sigma) [5][Nb][stride], 60 Nb B per ball), i.e. K = floor(3 Nb / 16), at
+// least 1 and at most F; a plan may fix the number.  The transient memory of
+// the 4D calls is then a fixed fraction of the model's, whatever the number
+// of frames.
+int frames_per_chunk(const pa_plan *plan, int n_basis, int F) {
   if (F <= 0) return 1;
   if (plan && plan->frames_per_chunk > 0) return std::min(plan->frames_per_chunk, F);
-  const long long per = std::max(1LL, 2LL * 5 * (long long)sizeof(float) * stride);
-  return (int)std::max(1LL, std::min<long long>(kChunkBudget / per, F));
+  return std::max(1, std::min(3 * n_basis / 16, F));
 }
 
 inline size_t round256(size_t b) { return (b + 255) & ~(size_t)255; }
@@ -933,7 +934,7 @@ size_t pa_forward_4d_workspace_size(const pa_geom *geom, const pa_canon *canon, 
   if (!tiles_ok(tiles)) return 0;
   const DevInfo *d = dev_info();
   if (!d) return 0;
-  const int K = frames_per_chunk(plan, canon->stride, n_frames);
+  const int K = frames_per_chunk(plan, canon->n_basis, n_frames);
   return chunk_state_bytes(canon, K) + forward_4d_partials(d, geom, canon, n_frames, K, tiles);
 }
 
@@ -957,7 +958,7 @@ int32_t pa_forward_4d(const pa_geom *geom, const pa_canon *canon, const float *t
     if (flags & PA_ACCUMULATE) return PA_OK;
     return cuda_status(cudaMemsetAsync(traces, 0, sizeof(float) * per_frame * n_frames, st));
   }
-  const int K = frames_per_chunk(plan, canon->stride, n_frames);
+  const int K = frames_per_chunk(plan, canon->n_basis, n_frames);
   const size_t sbytes = chunk_state_bytes(canon, K);
   const size_t need = sbytes + forward_4d_partials(d, geom, canon, n_frames, K, tiles);
   if (workspace == nullptr || workspace_bytes < need || !aligned(workspace, 256)) return PA_ERR_WORKSPACE;
@@ -978,7 +979,7 @@ int32_t pa_forward_4d(const pa_geom *geom, const pa_canon *canon, const float *t
 size_t pa_adjoint_4d_workspace_size(const pa_geom *geom, const pa_canon *canon, int32_t n_frames,
                                     const pa_plan *plan) {
   if (check_geom(geom) || check_canon(canon) || n_frames <= 0 || canon->n == 0) return 0;
-  const int K = frames_per_chunk(plan, canon->stride, n_frames);
+  const int K = frames_per_chunk(plan, canon->n_basis, n_frames);
   return 2 * chunk_state_bytes(canon, K);
 }
 
@@ -1007,7 +1008,7 @@ int32_t pa_adjoint_4d(const pa_geom *geom, const pa_canon *canon, const float *t
     if (e == cudaSuccess) e = cudaMemsetAsync(grads->sigma, 0, rows * 5 * canon->n_basis, st);
     return cuda_status(e);
   }
-  const int K = frames_per_chunk(plan, canon->stride, n_frames);
+  const int K = frames_per_chunk(plan, canon->n_basis, n_frames);
   const size_t sbytes = chunk_state_bytes(canon, K);
   if (workspace == nullptr || workspace_bytes < 2 * sbytes || !aligned(workspace, 256)) return PA_ERR_WORKSPACE;
   float *states = static_cast<float *>(workspace);

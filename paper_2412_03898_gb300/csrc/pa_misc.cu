@@ -9,9 +9,10 @@ namespace {
 
 constexpr int kFrameChunk = 8;
 
-// Eq. 1-2: one thread per (ball, chunk of up to kFrameChunk frames).  The
-// deformation parameters of a ball are read once per chunk; reads are
-// coalesced across threads (ball index fastest).
+// Eq. 1-2: one thread per (channel, ball, chunk of up to kFrameChunk
+// frames), so that even one frame gives 5 N threads.  The deformation
+// parameters of a (channel, ball) are read once per chunk, coalesced across
+// threads (ball index fastest), several basis functions' loads in flight.
 __global__ void __launch_bounds__(256) k_deform(const float *__restrict__ canon, const float *__restrict__ omega,
                                                 const float *__restrict__ theta, const float *__restrict__ sigma,
                                                 long long n, long long stride, int nb,
@@ -19,39 +20,41 @@ __global__ void __launch_bounds__(256) k_deform(const float *__restrict__ canon,
                                                 unsigned *err) {
   const float L2E_HALF = 0.72134752044448170368f;  // log2(e)/2
   const int nchunks = (F + kFrameChunk - 1) / kFrameChunk;
-  const long long total = n * nchunks;
+  const long long total = 5 * n * nchunks;
   bool dom = false;
   for (long long it = blockIdx.x * (long long)blockDim.x + threadIdx.x; it < total;
        it += (long long)gridDim.x * blockDim.x) {
     const long long b = it % n;
-    const int f0 = (int)(it / n) * kFrameChunk;
+    const long long r = it / n;
+    const int c = (int)(r % 5);
+    const int f0 = (int)(r / 5) * kFrameChunk;
     const int fc = min(kFrameChunk, F - f0);
     float tf[kFrameChunk];
 #pragma unroll
     for (int j = 0; j < kFrameChunk; ++j) tf[j] = j < fc ? __ldg(t + f0 + j) : 0.f;
-    for (int c = 0; c < 5; ++c) {
-      float H[kFrameChunk];
+    float H[kFrameChunk];
 #pragma unroll
-      for (int j = 0; j < kFrameChunk; ++j) H[j] = 0.f;
-      for (int k = 0; k < nb; ++k) {
-        const long long gi = ((long long)c * nb + k) * stride + b;
-        const float om = __ldg(omega + gi), th = __ldg(theta + gi), sg = __ldg(sigma + gi);
-        if (!(sg > 0.f)) {
-          dom = true;
-          continue;
-        }
-        const float is = 1.f / sg;
-#pragma unroll
-        for (int j = 0; j < kFrameChunk; ++j) {
-          const float d = (tf[j] - th) * is;
-          H[j] = fmaf(om, ex2(-d * d * L2E_HALF), H[j]);
-        }
+    for (int j = 0; j < kFrameChunk; ++j) H[j] = 0.f;
+    const long long g0 = (long long)c * nb * stride + b;
+#pragma unroll 4
+    for (int k = 0; k < nb; ++k) {
+      const long long gi = g0 + (long long)k * stride;
+      const float om = __ldg(omega + gi), th = __ldg(theta + gi), sg = __ldg(sigma + gi);
+      if (!(sg > 0.f)) {
+        dom = true;
+        continue;
       }
-      const float q0 = __ldg(canon + (long long)c * stride + b);
+      const float is = 1.f / sg;
 #pragma unroll
-      for (int j = 0; j < kFrameChunk; ++j)
-        if (j < fc) out[((long long)(f0 + j) * 5 + c) * stride + b] = q0 * (1.f + H[j]);
+      for (int j = 0; j < kFrameChunk; ++j) {
+        const float d = (tf[j] - th) * is;
+        H[j] = fmaf(om, ex2(-d * d * L2E_HALF), H[j]);
+      }
     }
+    const float q0 = __ldg(canon + (long long)c * stride + b);
+#pragma unroll
+    for (int j = 0; j < kFrameChunk; ++j)
+      if (j < fc) out[((long long)(f0 + j) * 5 + c) * stride + b] = q0 * (1.f + H[j]);
   }
   if (dom) set_error(err, PA_ERR_DOMAIN);
 }
@@ -87,6 +90,7 @@ __global__ void __launch_bounds__(256) k_deform_backward(const float *__restrict
     float gsum = 0.f;
     for (int f = 0; f < F; ++f) gsum += __ldg(gq + (long long)f * 5 * stride);
     float gcan = gsum;
+#pragma unroll 4
     for (int k = 0; k < nb; ++k) {
       const long long gi = ((long long)c * nb + k) * stride + b;
       const float om = __ldg(omega + gi), th = __ldg(theta + gi), sg = __ldg(sigma + gi);
@@ -253,7 +257,7 @@ cudaError_t launch_step_increment(int *step, cudaStream_t st) {
 cudaError_t launch_deform(const float *canon, const float *omega, const float *theta, const float *sigma,
                           long long n, long long stride, int nb, const float *t, int F, float *out, unsigned *err,
                           cudaStream_t st) {
-  const long long total = n * ((F + kFrameChunk - 1) / kFrameChunk);
+  const long long total = 5 * n * ((F + kFrameChunk - 1) / kFrameChunk);
   if (total == 0) return cudaSuccess;
   const long long blocks = std::min<long long>((total + 255) / 256, 152LL * 32);
   k_deform<<<(unsigned)blocks, 256, 0, st>>>(canon, omega, theta, sigma, n, stride, nb, t, F, out, err);

@@ -189,13 +189,13 @@ class GGBallIR:
         self.lr_scale = float(sd.get("lr_scale", self.lr_scale))
 
     def frames_per_chunk(self) -> int:
-        """Frames per launch of the 4D calls: the plan's, else as many as keep
-        one chunk's states and state gradients within 64 MiB (the library's
-        rule)."""
+        """Frames per launch of the 4D calls: the plan's, else the library's
+        rule, as many as keep one chunk's states and state gradients within an
+        eighth of the deformation parameters' memory: floor(3 Nb / 16)."""
         if self.plan is not None and self.plan.values()["frames_per_chunk"] > 0:
             return min(self.plan.values()["frames_per_chunk"], self.F)
-        per = 2 * 5 * 4 * int(self.canon.shape[-1])
-        return max(1, min(self.F, (64 << 20) // per))
+        nb = int(self.deform.shape[2])
+        return max(1, min(self.F, 3 * nb // 16))
 
     def launches_per_step(self, per_frame: bool = False) -> int:
         """Kernel launches of this library per iteration (memsets excluded)."""
