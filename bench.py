@@ -783,7 +783,9 @@ def bench_batched(args, pa, pa_inputs, dev, flush):
         b.grad_state = torch.empty_like(st)
         scenes.append(b)
     plan = tune_batched(scenes) if not args.no_autotune else None
-    ws = torch.empty(256, dtype=torch.uint8, device=dev)
+    arr = (pa._lib.pa_scene * len(scenes))(*[b.struct() for b in scenes])
+    ws = torch.empty(int(pa._LIB.pa_batched_workspace_size(arr, len(scenes), plan.handle if plan else None)),
+                     dtype=torch.uint8, device=dev)
     ws2 = torch.empty(256, dtype=torch.uint8, device=dev)
 
     def batched_step():

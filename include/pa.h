@@ -158,8 +158,9 @@ PA_API const char *pa_status_string(int32_t status);
  * the imaging calls (pa_ubp_filter, pa_ubp, pa_splat, pa_map, pa_ssim*) and
  * pa_selftest_bounded_wait.  2.00 added launch plans (pa_plan_*), the 4D
  * calls that recompute states per frame chunk (pa_forward_4d,
- * pa_adjoint_4d) and pa_measure_unit_rates, and changed pa_forward_batched
- * and pa_adjoint_batched to take a plan in place of a tile array. */
+ * pa_adjoint_4d) and pa_measure_unit_rates, changed pa_forward_batched and
+ * pa_adjoint_batched to take a plan in place of a tile array, and
+ * pa_batched_workspace_size to take the scenes and the plan. */
 PA_API int32_t pa_version(void);
 
 /* Reads, returns in *out (host) and clears the device error word of the
@@ -243,19 +244,25 @@ PA_API int32_t pa_adjoint(const pa_geom *geom, const pa_balls *balls, const pa_c
                    const float *t_frames, int32_t n_frames, const float *trace_grad,
                    const float *frame_scale, pa_grads *grads, uint32_t flags, void *stream);
 
-/* Scratch bytes a batched call needs (its work-queue counter). */
-PA_API size_t pa_batched_workspace_size(void);
+/* Scratch bytes the batched calls need for these scenes and this plan
+ * (NULL: the heuristic): the work-queue counter (256 bytes, all that
+ * pa_adjoint_batched uses) and, for pa_forward_batched, the partial traces
+ * [splits][F][S][T] of every scene it splits by balls. */
+PA_API size_t pa_batched_workspace_size(const pa_scene *scenes, int32_t n_scenes, const pa_plan *plan);
 
 /* Forward projection of several independent scenes of uneven ball, sensor,
  * sample and frame counts in one persistent launch (the batching of Sec. 1:
  * one cloud per scene for all its frames; several scenes per launch).  The
- * work items (scene, frame, sensor tile, sample tile) are taken from a
- * counter in the workspace, heaviest scenes first, by one CTA per SM.
- * Each scene's traces equal pa_forward's (same tiles, no ball splits).
- * scenes: host array of n_scenes (<= PA_MAX_SCENES); plan: its tiles (ball
- * splits ignored), or NULL for the heuristic; workspace: device, at least
- * pa_batched_workspace_size() bytes, 16-byte aligned.  Only the Gaussian
- * profile; flags: PA_ACCUMULATE. */
+ * work items (scene, frame, sensor tile, sample tile, ball split) are taken
+ * from a counter in the workspace, scenes with the most balls per split
+ * first, by one CTA per SM.  A scene is split into ball ranges (the plan's
+ * split count, else one per 131072 balls), whose partial traces are summed
+ * in split order afterwards with compensated additions; with one split its
+ * traces equal pa_forward_ex's with the same tiles and one split.
+ * scenes: host array of n_scenes (<= PA_MAX_SCENES); plan: tiles and split
+ * count, or NULL for the heuristic; workspace: device, 256-byte aligned, at
+ * least pa_batched_workspace_size(scenes, n_scenes, plan) bytes.  Only the
+ * Gaussian profile; flags: PA_ACCUMULATE. */
 PA_API int32_t pa_forward_batched(const pa_scene *scenes, int32_t n_scenes, uint32_t flags, const pa_plan *plan,
                                   void *workspace, size_t workspace_bytes, void *stream);
 

@@ -447,9 +447,9 @@ def forward_batched(scenes, tiles: Optional[Sequence[int]] = None, accumulate: b
         _check(sc.traces, "traces")
     arr = _scene_array(scenes)
     dev = scenes[0].state.device if scenes else torch.device("cuda")
-    if workspace is None:
-        workspace = torch.empty(int(_LIB.pa_batched_workspace_size()), dtype=torch.uint8, device=dev)
     h, keep = _plan_arg(plan, tiles)
+    need = int(_LIB.pa_batched_workspace_size(arr, len(scenes), h))
+    workspace = _workspace(workspace, need, dev)
     _lib.check(_LIB.pa_forward_batched(arr, len(scenes), _lib.PA_ACCUMULATE if accumulate else 0, h,
                                        workspace.data_ptr(), workspace.numel(), _stream()), "pa_forward_batched")
     del keep
@@ -467,8 +467,7 @@ def adjoint_batched(scenes, accumulate: bool = False, workspace: Optional[torch.
         _check(sc.grad_state, "grad_state")
     arr = _scene_array(scenes)
     dev = scenes[0].state.device if scenes else torch.device("cuda")
-    if workspace is None:
-        workspace = torch.empty(int(_LIB.pa_batched_workspace_size()), dtype=torch.uint8, device=dev)
+    workspace = _workspace(workspace, 256, dev)
     h = plan.handle if plan is not None else None
     _lib.check(_LIB.pa_adjoint_batched(arr, len(scenes), _lib.PA_ACCUMULATE if accumulate else 0, h,
                                        workspace.data_ptr(), workspace.numel(), _stream()), "pa_adjoint_batched")

@@ -260,6 +260,32 @@ constexpr int32_t kTileCandidates[][5] = {
 constexpr int kNumTileCandidates = sizeof(kTileCandidates) / sizeof(kTileCandidates[0]);
 constexpr int32_t kAdjChunkCandidates[] = {4, 8, 16, 32};
 
+// Bytes at the start of a batched call's workspace: its work-queue counter.
+constexpr size_t kQueueBytes = 256;
+
+// Ball splits of one scene in a batched forward: the plan's split count, else
+// one split per kMaxBallsPerSplit balls (narrower arrival bands per split), at
+// most one per TMA stage of balls; balls per split a multiple of 4.
+void batched_splits(long long n, const int32_t *tiles, int nb_tile, int &n_splits, long long &bps) {
+  long long sp = tiles && tiles[3] > 0 ? tiles[3] : (n + pa::kMaxBallsPerSplit - 1) / pa::kMaxBallsPerSplit;
+  sp = std::max(1LL, std::min(sp, (n + nb_tile - 1) / nb_tile));
+  bps = (((n + sp - 1) / sp) + 3) & ~3LL;
+  if (bps <= 0) bps = 4;
+  n_splits = (int)std::max(1LL, (n + bps - 1) / bps);
+}
+
+int batched_nb_tile(const int32_t *tiles) { return tiles && tiles[2] > 0 ? tiles[2] : 512; }
+
+// Split partials [splits][F][S][T] of one scene of a batched forward.
+size_t batched_partial_bytes(const pa_scene &sc, const int32_t *tiles) {
+  if (sc.n_frames <= 0 || sc.balls.n <= 0) return 0;
+  int sp;
+  long long bps;
+  batched_splits(sc.balls.n, tiles, batched_nb_tile(tiles), sp, bps);
+  if (sp <= 1) return 0;
+  return round256(sizeof(float) * (size_t)sp * sc.n_frames * sc.geom.n_sensors * sc.geom.n_samples);
+}
+
 int check_scenes(const pa_scene *scenes, int32_t n_scenes) {
   if (n_scenes < 1 || n_scenes > PA_MAX_SCENES || scenes == nullptr) return PA_ERR_INVALID_ARG;
   for (int i = 0; i < n_scenes; ++i) {
@@ -448,7 +474,13 @@ int32_t pa_adjoint(const pa_geom *geom, const pa_balls *balls, const pa_canon *c
   return cuda_status(pa::launch_adjoint_static(a, d->sms, st));
 }
 
-size_t pa_batched_workspace_size(void) { return 256; }
+size_t pa_batched_workspace_size(const pa_scene *scenes, int32_t n_scenes, const pa_plan *plan) {
+  size_t ws = kQueueBytes;
+  if (n_scenes <= 0 || scenes == nullptr || n_scenes > PA_MAX_SCENES) return ws;
+  const int32_t *tiles = plan ? plan->tiles : nullptr;
+  for (int i = 0; i < n_scenes; ++i) ws += batched_partial_bytes(scenes[i], tiles);
+  return ws;
+}
 
 int32_t pa_forward_batched(const pa_scene *scenes, int32_t n_scenes, uint32_t flags, const pa_plan *plan,
                            void *workspace, size_t workspace_bytes, void *stream) {
@@ -456,8 +488,6 @@ int32_t pa_forward_batched(const pa_scene *scenes, int32_t n_scenes, uint32_t fl
   if (n_scenes < 0 || n_scenes > PA_MAX_SCENES || (n_scenes > 0 && scenes == nullptr)) return PA_ERR_INVALID_ARG;
   if ((flags & ~PA_ACCUMULATE) != 0) return PA_ERR_INVALID_ARG;
   if (!tiles_ok(tiles)) return PA_ERR_INVALID_ARG;
-  if (workspace == nullptr || workspace_bytes < pa_batched_workspace_size() || !aligned(workspace, 16))
-    return PA_ERR_WORKSPACE;
   const DevInfo *d = dev_info();
   if (!d) return PA_ERR_CUDA;
   cudaStream_t st = static_cast<cudaStream_t>(stream);
@@ -478,7 +508,10 @@ int32_t pa_forward_batched(const pa_scene *scenes, int32_t n_scenes, uint32_t fl
   const int group = tiles && (tiles[4] == 1 || tiles[4] == 2 || tiles[4] == 4 || tiles[4] == 8) ? tiles[4] : 16;
   const size_t smem = pa::forward_smem_bytes(s_tile, t_tile, nb_tile);
   if ((long long)smem > d->max_smem) return PA_ERR_INVALID_ARG;
-  // scenes with balls, heaviest items (most balls) first
+  if (workspace == nullptr || workspace_bytes < pa_batched_workspace_size(scenes, n_scenes, plan) ||
+      !aligned(workspace, 256))
+    return PA_ERR_WORKSPACE;
+  // scenes with balls, heaviest items (most balls per split) first
   int order[PA_MAX_SCENES];
   int m = 0;
   for (int i = 0; i < n_scenes; ++i) {
@@ -494,7 +527,13 @@ int32_t pa_forward_batched(const pa_scene *scenes, int32_t n_scenes, uint32_t fl
     }
     order[m++] = i;
   }
-  std::sort(order, order + m, [&](int x, int y) { return scenes[x].balls.n > scenes[y].balls.n; });
+  auto item_balls = [&](int i) {
+    int sp;
+    long long bps;
+    batched_splits(scenes[i].balls.n, tiles, nb_tile, sp, bps);
+    return std::min<long long>(bps, scenes[i].balls.n);
+  };
+  std::sort(order, order + m, [&](int x, int y) { return item_balls(x) > item_balls(y); });
   pa::BatchFwdArgs a;
   std::memset(&a, 0, sizeof(a));
   a.n_scenes = m;
@@ -505,6 +544,7 @@ int32_t pa_forward_batched(const pa_scene *scenes, int32_t n_scenes, uint32_t fl
   a.flags = flags;
   a.err = d->err;
   long long items = 0;
+  char *partials = static_cast<char *>(workspace) + kQueueBytes;
   for (int j = 0; j < m; ++j) {
     const pa_scene &sc = scenes[order[j]];
     pa::SceneFwd &o = a.sc[j];
@@ -512,17 +552,26 @@ int32_t pa_forward_batched(const pa_scene *scenes, int32_t n_scenes, uint32_t fl
     o.state = sc.balls.state;
     o.n = sc.balls.n;
     o.stride = sc.balls.stride;
+    o.F = sc.n_frames;
     o.out = sc.traces;
     o.n_stiles = (sc.geom.n_sensors + s_tile - 1) / s_tile;
     o.n_ttiles = (sc.geom.n_samples + t_tile - 1) / t_tile;
+    batched_splits(sc.balls.n, tiles, nb_tile, o.n_splits, o.balls_per_split);
+    o.partial = nullptr;
+    if (o.n_splits > 1) {
+      o.partial = reinterpret_cast<float *>(partials);
+      partials += batched_partial_bytes(sc, tiles);
+    }
     o.item_begin = items;
-    items += (long long)sc.n_frames * o.n_stiles * o.n_ttiles;
+    items += (long long)sc.n_frames * o.n_stiles * o.n_ttiles * o.n_splits;
   }
   a.total_items = items;
   if (items == 0) return PA_OK;
-  // CTAs write only the sample band a scene's balls reach: zero the rest first
+  // CTAs write only the sample band a scene's balls reach: zero the rest
+  // first (scenes with ball splits are written whole by the split reduction)
   if (!(flags & PA_ACCUMULATE)) {
     for (int j = 0; j < m; ++j) {
+      if (a.sc[j].n_splits > 1) continue;
       const pa_scene &sc = scenes[order[j]];
       cudaError_t e = cudaMemsetAsync(
           sc.traces, 0, sizeof(float) * (size_t)sc.n_frames * sc.geom.n_sensors * sc.geom.n_samples, st);
@@ -536,8 +585,7 @@ int32_t pa_adjoint_batched(const pa_scene *scenes, int32_t n_scenes, uint32_t fl
                            void *workspace, size_t workspace_bytes, void *stream) {
   if (n_scenes < 0 || n_scenes > PA_MAX_SCENES || (n_scenes > 0 && scenes == nullptr)) return PA_ERR_INVALID_ARG;
   if ((flags & ~PA_ACCUMULATE) != 0) return PA_ERR_INVALID_ARG;
-  if (workspace == nullptr || workspace_bytes < pa_batched_workspace_size() || !aligned(workspace, 16))
-    return PA_ERR_WORKSPACE;
+  if (workspace == nullptr || workspace_bytes < kQueueBytes || !aligned(workspace, 16)) return PA_ERR_WORKSPACE;
   const DevInfo *d = dev_info();
   if (!d) return PA_ERR_CUDA;
   int order[PA_MAX_SCENES];
@@ -777,8 +825,16 @@ int32_t pa_measure_unit_rates(void *stream, double *out4) {
 
 size_t pa_plan_workspace_size(const pa_scene *scenes, int32_t n_scenes) {
   if (check_scenes(scenes, n_scenes)) return 0;
-  size_t ws = pa_batched_workspace_size();
-  if (n_scenes > 1) return ws;
+  size_t ws = kQueueBytes;
+  if (n_scenes > 1) {
+    for (int c = -1; c < kNumTileCandidates; ++c) {
+      pa_plan p;
+      std::memset(&p, 0, sizeof(p));
+      if (c >= 0) std::memcpy(p.tiles, kTileCandidates[c], sizeof(p.tiles));
+      ws = std::max(ws, pa_batched_workspace_size(scenes, n_scenes, &p));
+    }
+    return ws;
+  }
   const DevInfo *d = dev_info();
   if (!d) return 0;
   const pa_scene &sc = scenes[0];

@@ -38,7 +38,6 @@ namespace pa {
 namespace {
 
 constexpr int kMaxThreads = 512;  // at most 16 sensors (warps) per CTA
-constexpr long long kMaxBallsPerSplit = 131072;  // default plans split larger ball sets
 
 constexpr int kRowPad = 32;   // samples of padding after every trace row
 constexpr int kClasses = 17;  // 16 radius classes + 1 for slots past the tile's end
@@ -542,9 +541,10 @@ __global__ void __launch_bounds__(kMaxThreads, 1) k_forward(const FwdArgs A) {
 }
 
 // Persistent CTAs over the work items of several scenes: an item is
-// (scene, frame, sensor tile, sample tile), taken from a global counter in
-// the order of the scene table (the host orders scenes by item cost,
-// heaviest first).
+// (scene, frame, sensor tile, sample tile, ball split), taken from a global
+// counter in the order of the scene table (the host orders scenes by item
+// cost, heaviest first).  A scene with several ball splits writes partial
+// traces that the host sums afterwards (k_reduce_splits, split order).
 template <int G>
 __global__ void __launch_bounds__(kMaxThreads, 1) k_forward_batched(const BatchFwdArgs A) {
   extern __shared__ __align__(128) unsigned char smem_raw[];
@@ -561,20 +561,26 @@ __global__ void __launch_bounds__(kMaxThreads, 1) k_forward_batched(const BatchF
     while (sc + 1 < A.n_scenes && item >= A.sc[sc + 1].item_begin) ++sc;
     const SceneFwd &d = A.sc[sc];
     long long local = item - d.item_begin;
+    const int split = (int)(local % d.n_splits);
+    local /= d.n_splits;
     const int tt = (int)(local % d.n_ttiles);
     local /= d.n_ttiles;
     const int st = (int)(local % d.n_stiles);
     const int f = (int)(local / d.n_stiles);
-    const float *state_f0 = d.state + (long long)f * 5 * d.stride;
+    const long long b_begin = (long long)split * d.balls_per_split;
+    const long long b_end = min(d.n, b_begin + d.balls_per_split);
+    const float *state_f = d.state + (long long)f * 5 * d.stride;
     bool whole;
-    const int k0 = band_tile_start<false>(d.q, state_f0, d.stride, 0, d.n, A.s_tile, st, A.t_tile, tt,
+    const int k0 = band_tile_start<false>(d.q, state_f, d.stride, b_begin, b_end, A.s_tile, st, A.t_tile, tt,
                                           m.sgrp, whole);
-    if (k0 < 0) continue;  // no arrival in this tile; the traces were zeroed
+    if (k0 < 0) continue;  // no arrival in this tile; the outputs were zeroed
     const int klen = min(A.t_tile, d.q.T - k0);
-    const bool ok = forward_item<false, G>(d.q, d.state + (long long)f * 5 * d.stride, d.stride, 0, d.n, A.s_tile,
-                                           A.t_tile, A.nb_tile, st, k0, klen, !whole,
-                                           d.out + (long long)f * d.q.S * d.q.T,
-                                           (A.flags & PA_ACCUMULATE) != 0, m, phase, A.err);
+    const long long frame = (long long)d.q.S * d.q.T;
+    const bool single = d.n_splits == 1;
+    float *dst = single ? d.out + f * frame : d.partial + ((long long)split * d.F + f) * frame;
+    const bool ok = forward_item<false, G>(d.q, state_f, d.stride, b_begin, b_end, A.s_tile, A.t_tile, A.nb_tile,
+                                           st, k0, klen, !whole, dst, single && (A.flags & PA_ACCUMULATE) != 0, m,
+                                           phase, A.err);
     if (!ok) break;
   }
 }
@@ -759,9 +765,27 @@ cudaError_t launch_forward_batched(const BatchFwdArgs &a, int group, size_t smem
   if (occ < 1) return cudaErrorInvalidConfiguration;
   e = cudaMemsetAsync(a.counter, 0, sizeof(unsigned long long), st);
   if (e != cudaSuccess) return e;
+  // CTAs write only the sample band a split's balls reach: zero the partials
+  for (int j = 0; j < a.n_scenes && e == cudaSuccess; ++j) {
+    const SceneFwd &d = a.sc[j];
+    if (d.n_splits > 1)
+      e = cudaMemsetAsync(d.partial, 0, sizeof(float) * (size_t)d.n_splits * d.F * d.q.S * d.q.T, st);
+  }
+  if (e != cudaSuccess) return e;
   const long long grid = std::max(1LL, std::min(a.total_items, (long long)sms * occ));
   fn<<<(unsigned)grid, 32 * a.s_tile, smem, st>>>(a);
-  return cudaGetLastError();
+  if ((e = cudaGetLastError()) != cudaSuccess) return e;
+  for (int j = 0; j < a.n_scenes; ++j) {
+    const SceneFwd &d = a.sc[j];
+    if (d.n_splits <= 1) continue;
+    const long long n4 = (long long)d.F * d.q.S * d.q.T / 4;
+    const long long blocks = std::min<long long>((n4 + 255) / 256, 152LL * 16);
+    k_reduce_splits<<<(unsigned)std::max(1LL, blocks), 256, 0, st>>>(
+        reinterpret_cast<const float4 *>(d.partial), reinterpret_cast<float4 *>(d.out), n4, d.n_splits,
+        (a.flags & PA_ACCUMULATE) != 0);
+    if ((e = cudaGetLastError()) != cudaSuccess) return e;
+  }
+  return cudaSuccess;
 }
 
 cudaError_t launch_count(const Acq &q, const float *state, long long n, long long stride, int F,

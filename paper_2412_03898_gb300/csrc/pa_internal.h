@@ -35,6 +35,9 @@ struct FwdArgs {
   unsigned *err;
 };
 
+// Default plans split larger ball sets (narrower arrival bands per split).
+constexpr long long kMaxBallsPerSplit = 131072;
+
 // Batched (several scenes, one persistent launch).
 constexpr int kMaxScenes = 64;
 
@@ -42,8 +45,11 @@ struct SceneFwd {
   Acq q;
   const float *state;
   long long n, stride;
+  int F;
   float *out;
-  int n_stiles, n_ttiles;
+  float *partial;              // [n_splits][F][S][T] when n_splits > 1
+  int n_stiles, n_ttiles, n_splits;
+  long long balls_per_split;
   long long item_begin;  // first work item of this scene
 };
 
