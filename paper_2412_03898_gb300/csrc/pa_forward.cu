@@ -124,7 +124,7 @@ __device__ __forceinline__ void order_tile(const float *ba, int nbt, int cnt, in
 }
 
 // Group records in a warp's 128-float area (16-byte aligned).  G >= 2: per
-// group, H = G/2 float4 (u_x, u_y, -du_x, -du_y) of ball pairs, H float2
+// group, H = G/2 float4 (u_x, u_y, -32 du_x, -32 du_y) of ball pairs, H float2
 // (amp_x, amp_y), then (first sample, step count) as ints; stride rounded up
 // to 4 floats.  G = 1: one float4 (u, -du, amp, first | steps << 16) each.
 template <int G>
@@ -263,7 +263,7 @@ __device__ __forceinline__ bool forward_item(const Acq &q, const float *state_f,
           const int j = pos & 15;
           float *r = mygrp + (pos >> 4) * GS;
           r[(j >> 1) * 4 + (j & 1)] = us;
-          r[(j >> 1) * 4 + 2 + (j & 1)] = nd;
+          r[(j >> 1) * 4 + 2 + (j & 1)] = 32.f * nd;  // one 32-sample step
           r[4 * H + j] = am;
           if (j == 0) reinterpret_cast<int2 *>(r + 6 * H)[0] = make_int2(kmin, nsteps);
         } else {
@@ -295,13 +295,14 @@ __device__ __forceinline__ bool forward_item(const Acq &q, const float *state_f,
             const int j = lane & (G - 1);
             float *r = mygrp + (lane / G) * GS;
             r[(j >> 1) * 4 + (j & 1)] = us;
-            r[(j >> 1) * 4 + 2 + (j & 1)] = nd;
+            r[(j >> 1) * 4 + 2 + (j & 1)] = 32.f * nd;  // one 32-sample step
             r[4 * H + j] = am;
             if (j == 0) reinterpret_cast<int2 *>(r + 6 * H)[0] = make_int2(kmin, nsteps);
           }
         }
         __syncwarp();
         const float lf = (float)lane;
+        const float lf32 = lf * 0.03125f;  // lane / 32, exact
         for (int g0 = 0; g0 < nv; g0 += G) {
           // balls in twos: u, its step and amp*u of two balls share one packed
           // FP32x2 instruction; u starts at this lane's first sample
@@ -318,10 +319,12 @@ __device__ __forceinline__ bool forward_item(const Acq &q, const float *state_f,
             const float *r = mygrp + (g0 / G) * GS;
 #pragma unroll
             for (int h = 0; h < H; ++h) {
+              // the record holds 32 x (-du); (lane / 32) x that is exactly
+              // lane x (-du), so u starts at this lane's sample exactly
               const float4 ud = reinterpret_cast<const float4 *>(r)[h];
-              const float2 ndh = make_float2(ud.z, ud.w);
-              u2[h] = __ffma2_rn(make_float2(lf, lf), ndh, make_float2(ud.x, ud.y));
-              nd2[h] = __fmul2_rn(make_float2(32.f, 32.f), ndh);
+              const float2 nd32 = make_float2(ud.z, ud.w);
+              u2[h] = __ffma2_rn(make_float2(lf32, lf32), nd32, make_float2(ud.x, ud.y));
+              nd2[h] = nd32;
               amp2[h] = reinterpret_cast<const float2 *>(r + 4 * H)[h];
             }
             const int2 kn = reinterpret_cast<const int2 *>(r + 6 * H)[0];
