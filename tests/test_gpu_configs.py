@@ -74,8 +74,8 @@ def test_4d_100k_20f_ir_path_sampled(pa):
 
 def test_batched_16_sampled(pa):
     """The 16 uneven scenes as one persistent forward (with the tiles the
-    autotuner picks, as timed) and one persistent adjoint; per scene, 2
-    sampled sensors' traces and 8 sampled balls' gradients of one frame
+    autotuner picks, as timed) and one persistent adjoint; per scene, 6
+    sampled sensors' traces and 24 sampled balls' gradients of one frame
     against the oracle."""
     from paper_2412_03898_gb300.autotune import tune_batched
     rng = np.random.default_rng(73)
@@ -96,10 +96,10 @@ def test_batched_16_sampled(pa):
     for sc, b in zip(raw, scenes):
         states = sc.frames if sc.frames is not None else sc.balls[None]
         f = int(rng.integers(b.F))
-        pick_s = np.sort(rng.choice(sc.n_sensors, 2, replace=False))
+        pick_s = np.sort(rng.choice(sc.n_sensors, 6, replace=False))
         y_o, _ = oracle.forward(states[f], sc.sensors[:, pick_s], sc.c, sc.fs, sc.t0, sc.n_samples, sc.kappa)
         assert rel_l2(b.traces[f, pick_s].cpu().numpy(), y_o[0]) <= TRACE_TOL, sc.name
-        pick = np.sort(rng.choice(sc.n_balls, 8, replace=False))
+        pick = np.sort(rng.choice(sc.n_balls, 24, replace=False))
         g = b.trace_grad[f:f + 1].cpu().numpy()
         want = oracle.adjoint_state(states[f][None][:, :, pick], sc.sensors, sc.c, sc.fs, sc.t0, sc.n_samples,
                                     sc.kappa, g)

@@ -2,9 +2,9 @@
 on an 80 mm hemisphere, 4096 samples, 50 frames, Nb = 65) in the launch
 configuration the IR uses for it (pa_forward_4d / pa_adjoint_4d, states
 recomputed per frame chunk), and through the fused 4D adjoint, checked on
-sampled outputs the FP64 oracle can compute one by one: traces of 8 random
-sensors at the first and last frame, and the 4D gradients of 32 random balls
-for a residual that is non-zero on those two frames (the oracle sums its
+sampled outputs the FP64 oracle can compute one by one: traces of 24 random
+sensors at the first, middle and last frame, and the 4D gradients of 96
+random balls for a residual that is non-zero on those three frames (the oracle sums its
 per-frame gradients, which the chain rule of Eq. 1-2 makes exact)."""
 import numpy as np
 import pytest
@@ -31,8 +31,8 @@ def test_large_4d_sampled_parity():
     t_dev = torch.from_numpy(t).cuda()
     traces = pa.forward_4d(geom, canon, deform, t_dev, n)
     pa.device_error()
-    frames = [0, F - 1]
-    pick_s = np.sort(rng.choice(sc.n_sensors, 8, replace=False))
+    frames = [0, F // 2, F - 1]
+    pick_s = np.sort(rng.choice(sc.n_sensors, 24, replace=False))
     # pa_forward over all 50 frames' stored states: split partials bounded at
     # 1 GiB by frame chunks inside the call
     state = pa.deform_balls(canon, omega, theta, sigma, t_dev, n)
@@ -53,7 +53,7 @@ def test_large_4d_sampled_parity():
     g_host = {f: rng.standard_normal((1, sc.n_sensors, sc.n_samples)).astype(np.float32) for f in frames}
     for f in frames:
         g[f] = torch.from_numpy(g_host[f][0]).cuda()
-    pick = np.sort(rng.choice(n, 32, replace=False))
+    pick = np.sort(rng.choice(n, 96, replace=False))
     want = None
     for f in frames:
         w = oracle.adjoint_4d(sc.balls[:, pick], om[:, :, pick], th[:, :, pick], sg[:, :, pick], t[f:f + 1],
