@@ -305,6 +305,25 @@ size_t batched_partial_bytes(const pa_scene &sc, const int32_t *tiles) {
   return round256(sizeof(float) * (size_t)sp * sc.n_frames * sc.geom.n_sensors * sc.geom.n_samples);
 }
 
+// Tile shape of a batched forward over these scenes: samples per CTA capped by
+// the longest trace, then the sensors per CTA that fit.
+struct BatchedTiles {
+  int s_tile, t_tile, nb_tile, group;
+  size_t smem;
+};
+BatchedTiles batched_tiles(const pa_scene *scenes, int32_t n_scenes, const int32_t *tiles) {
+  int maxT = 4;
+  for (int i = 0; i < n_scenes; ++i) maxT = std::max(maxT, scenes[i].geom.n_samples);
+  BatchedTiles b;
+  b.t_tile = tiles && tiles[1] > 0 ? tiles[1] : pa::kDefaultTTile;
+  b.t_tile = std::min(std::min(b.t_tile, maxT), 16384);
+  b.nb_tile = tiles && tiles[2] > 0 ? tiles[2] : 512;
+  b.s_tile = tiles && tiles[0] > 0 ? tiles[0] : pa::forward_default_s_tile(b.t_tile, b.nb_tile);
+  b.group = tiles && (tiles[4] == 1 || tiles[4] == 2 || tiles[4] == 4 || tiles[4] == 8) ? tiles[4] : 16;
+  b.smem = pa::forward_smem_bytes(b.s_tile, b.t_tile, b.nb_tile);
+  return b;
+}
+
 int check_scenes(const pa_scene *scenes, int32_t n_scenes) {
   if (n_scenes < 1 || n_scenes > PA_MAX_SCENES || scenes == nullptr) return PA_ERR_INVALID_ARG;
   for (int i = 0; i < n_scenes; ++i) {
@@ -510,7 +529,6 @@ int32_t pa_forward_batched(const pa_scene *scenes, int32_t n_scenes, uint32_t fl
   const DevInfo *d = dev_info();
   if (!d) return PA_ERR_CUDA;
   cudaStream_t st = static_cast<cudaStream_t>(stream);
-  int maxT = 4;
   for (int i = 0; i < n_scenes; ++i) {
     const pa_scene &sc = scenes[i];
     int rc = check_geom(&sc.geom);
@@ -518,14 +536,10 @@ int32_t pa_forward_batched(const pa_scene *scenes, int32_t n_scenes, uint32_t fl
     if ((rc = check_balls(&sc.balls))) return rc;
     if (sc.n_frames < 0) return PA_ERR_INVALID_ARG;
     if (sc.n_frames > 0 && (sc.traces == nullptr || !aligned(sc.traces, 16))) return PA_ERR_INVALID_ARG;
-    maxT = std::max(maxT, sc.geom.n_samples);
   }
-  int t_tile = tiles && tiles[1] > 0 ? tiles[1] : pa::kDefaultTTile;
-  t_tile = std::min(std::min(t_tile, maxT), 16384);
-  const int nb_tile = tiles && tiles[2] > 0 ? tiles[2] : 512;
-  const int s_tile = tiles && tiles[0] > 0 ? tiles[0] : pa::forward_default_s_tile(t_tile, nb_tile);
-  const int group = tiles && (tiles[4] == 1 || tiles[4] == 2 || tiles[4] == 4 || tiles[4] == 8) ? tiles[4] : 16;
-  const size_t smem = pa::forward_smem_bytes(s_tile, t_tile, nb_tile);
+  const BatchedTiles bt = batched_tiles(scenes, n_scenes, tiles);
+  const int t_tile = bt.t_tile, nb_tile = bt.nb_tile, s_tile = bt.s_tile, group = bt.group;
+  const size_t smem = bt.smem;
   if ((long long)smem > d->max_smem) return PA_ERR_INVALID_ARG;
   if (workspace == nullptr || workspace_bytes < pa_batched_workspace_size(scenes, n_scenes, plan) ||
       !aligned(workspace, 256))
@@ -928,8 +942,10 @@ int32_t pa_plan_create(const pa_scene *scenes, int32_t n_scenes, uint32_t flags,
   bool cand_ok[kNumTileCandidates + 1];
   for (int c = -1; c < kNumTileCandidates; ++c) {
     const int32_t *t = c < 0 ? nullptr : kTileCandidates[c];
-    const pa::FwdPlan p0 = plan_for(d, &scenes[0].geom, std::max<long long>(scenes[0].balls.n, 1), 1, t);
-    cand_ok[c + 1] = p0.smem <= (size_t)d->max_smem;
+    const size_t smem = n_scenes == 1
+                            ? plan_for(d, &scenes[0].geom, std::max<long long>(scenes[0].balls.n, 1), 1, t).smem
+                            : batched_tiles(scenes, n_scenes, t).smem;
+    cand_ok[c + 1] = smem <= (size_t)d->max_smem;
     cand_ms[c + 1] = 3.4e38f;
   }
   auto run_candidate = [&](int c) {

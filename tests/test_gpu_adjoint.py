@@ -206,3 +206,44 @@ def test_adjoint_wide_and_float4_walks_agree(pa):
         assert rel_l2(wide[:, ch], want[:, ch]) <= GRAD_TOL, ch
         assert rel_l2(narrow[:, ch], want[:, ch]) <= GRAD_TOL, ch
         assert rel_l2(wide[:, ch], narrow[:, ch]) <= 1e-5, ch
+
+
+def test_4d_calls_chunks_edges_and_accumulate(pa):
+    """pa_forward_4d equals pa_deform_balls + pa_forward_ex per frame chunk (the
+    same launches), for chunk sizes that do and do not divide F and larger
+    than F; pa_adjoint_4d accumulates; empty clouds and zero frames."""
+    rng = np.random.default_rng(91)
+    n, nb, F = 211, 5, 7
+    sc = pa_inputs.small_scene(seed=91, n_balls=n, n_sensors=9, n_samples=516)
+    om, th, sg = pa_inputs.random_deform(n, nb, rng)
+    geom = geometry(sc)
+    t = torch.from_numpy(pa_inputs.frame_times(F)).cuda()
+    canon = dev_pad(sc.balls)
+    deform = torch.stack([dev_pad(x) for x in (om, th, sg)])
+    g = torch.from_numpy(rng.standard_normal((F, 9, 516)).astype(np.float32)).cuda()
+    ref_gc, ref_gd = None, None
+    for K in (1, 3, 7, 20):
+        plan = pa.Plan.from_values(frames_per_chunk=K)
+        y = pa.forward_4d(geom, canon, deform, t, n, plan=plan)
+        for f0 in range(0, F, K):
+            k = min(K, F - f0)
+            st = pa.deform_balls(canon, deform[0], deform[1], deform[2], t[f0:f0 + k].contiguous(), n)
+            assert torch.equal(y[f0:f0 + k], pa.forward(geom, st, n)), (K, f0)
+        gc, gd = pa.adjoint_4d(geom, g, canon, deform, t, n, plan=plan)
+        if ref_gc is None:
+            ref_gc, ref_gd = gc, gd
+        else:  # chunking changes only the order of the per-chunk sums
+            torch.testing.assert_close(gc[:, :n], ref_gc[:, :n], rtol=1e-5, atol=1e-6 * float(ref_gc.abs().max()))
+            torch.testing.assert_close(gd[..., :n], ref_gd[..., :n], rtol=1e-5, atol=1e-6 * float(ref_gd.abs().max()))
+    gc2, gd2 = pa.adjoint_4d(geom, g, canon, deform, t, n, out=(ref_gc.clone(), ref_gd.clone()), accumulate=True)
+    # (padding columns past n are never written)
+    torch.testing.assert_close(gc2[:, :n], 2 * ref_gc[:, :n], rtol=1e-6, atol=1e-7 * float(ref_gc[:, :n].abs().max()))
+    torch.testing.assert_close(gd2[..., :n], 2 * ref_gd[..., :n], rtol=1e-6,
+                               atol=1e-7 * float(ref_gd[..., :n].abs().max()))
+    # empty cloud: zero traces, nothing to accumulate; zero frames: zero gradients
+    y0 = pa.forward_4d(geom, canon, deform, t, 0)
+    assert not torch.any(y0)
+    z = pa.adjoint_4d(geom, g[:0].contiguous(), canon, deform, t[:0].contiguous(), n,
+                      out=(torch.full_like(canon, 5.0), torch.full_like(deform, 5.0)))
+    assert not torch.any(z[0][:, :n]) and not torch.any(z[1][..., :n])
+    pa.device_error()

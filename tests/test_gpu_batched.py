@@ -155,3 +155,21 @@ def test_single_scene_plan_and_autotune_cache(pa, tmp_path, monkeypatch):
     monkeypatch.setattr(autotune, "_cache", {})
     again = autotune.tune_forward_plan(geom, st, sc.n_balls)  # from the file, not re-timed
     assert again.values()["tiles"] == v["tiles"] and not again.values()["tuned"]
+
+
+def test_forward_batched_ball_splits_equal_single_and_accumulate(pa):
+    """With ball splits (partials in the workspace, summed in split order)
+    every scene's traces equal pa_forward_ex's with the same tiles and split
+    count bit for bit; accumulate adds onto existing traces."""
+    tiles = (16, 1536, 256, 3, 16)
+    scs = _scenes()
+    batch = [pa.Scene(geometry(sc), dev_pad(_states(sc)), sc.n_balls) for sc in scs]
+    pa.forward_batched(batch, tiles=tiles)
+    pa.device_error()
+    for sc, b in zip(scs, batch):
+        single = pa.forward(geometry(sc), dev_pad(_states(sc)), sc.n_balls, tiles=tiles)
+        assert torch.equal(b.traces, single), sc.name
+    first = [b.traces.clone() for b in batch]
+    pa.forward_batched(batch, tiles=tiles, accumulate=True)
+    for f0, b in zip(first, batch):
+        torch.testing.assert_close(b.traces, 2 * f0, rtol=1e-6, atol=1e-7 * float(f0.abs().max()))
