@@ -48,7 +48,7 @@ __device__ __forceinline__ void ball_frame_grad(const Acq &q, const float *gfram
                                                 float4 *rec, int lane, float bx, float by, float bz, float a,
                                                 float p, float out[5], bool &dom) {
   const int S = q.S, T = q.T;
-  const float mbias = window_bias((q.kappa * K_S) * (q.kappa * K_S));
+  const float umax2 = (q.kappa * K_S) * (q.kappa * K_S);  // the forward's window test u^2 <= umax2
   // 256-bit residual loads need 32-byte aligned rows
   const bool wide = ALLOW_WIDE && (T & 7) == 0 && (reinterpret_cast<uintptr_t>(gframe) & 31) == 0;
   float gx = 0.f, gy = 0.f, gz = 0.f, ga = 0.f, gp = 0.f;
@@ -88,7 +88,7 @@ __device__ __forceinline__ void ball_frame_grad(const Acq &q, const float *gfram
       // arithmetic.  All pairs belong to one ball, so their windows have
       // nearly the same length and the sub-warps finish together.  Samples
       // of the aligned loads outside the window get weight 0 from the window
-      // mask (u^2 <= (kappa K_S)^2, the forward's own test).
+      // test (u^2 <= (kappa K_S)^2, the forward's own test).
       const int sub = lane >> 1, sl = lane & 1;
       const float2 negk = make_float2(-K_2LN2, -K_2LN2), one = make_float2(1.f, 1.f);
       for (int g0 = 0; g0 < nv; g0 += 16) {
@@ -115,9 +115,10 @@ __device__ __forceinline__ void ball_frame_grad(const Acq &q, const float *gfram
         float2 S1 = make_float2(0.f, 0.f), S3 = S1, SR = S1;
         auto half = [&](const float2 u2, const float2 g2) {
           const float2 sq = __fmul2_rn(u2, u2);                                      // u^2
-          const float2 msk = make_float2(window_mask(sq.x, mbias), window_mask(sq.y, mbias));
-          const float2 E = make_float2(ex2(-sq.x), ex2(-sq.y));                      // exp(-tau^2/(2a^2))
-          const float2 ge = __fmul2_rn(__fmul2_rn(g2, msk), E);
+          // exp(-tau^2/(2a^2)) inside the window, 0 outside it (compare and
+          // select on the ALU pipe, which has room; the FMA pipe has not)
+          const float2 E = make_float2(sq.x <= umax2 ? ex2(-sq.x) : 0.f, sq.y <= umax2 ? ex2(-sq.y) : 0.f);
+          const float2 ge = __fmul2_rn(g2, E);
           const float2 gu = __fmul2_rn(ge, u2);
           S1 = __fadd2_rn(S1, gu);                                                   // sum g E u
           S3 = __ffma2_rn(gu, sq, S3);                                               // sum g E u^3

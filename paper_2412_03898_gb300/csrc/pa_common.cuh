@@ -18,19 +18,6 @@ constexpr float K_S = 0.849321800288019f;
 // 2 ln 2: 1 - tau^2/a^2 = 1 - 2 ln2 * u^2.
 constexpr float K_2LN2 = 1.3862943611198906f;
 
-// Window mask of one sample in one saturated FMA, equal to (u^2 <= umax2):
-// with U the next float above umax2, sat(2^64 (U - u^2)) is 1 for every
-// u^2 <= umax2 (the gap is at least one ulp of U >= 2^-24, so the scaled
-// difference is >= 2^40), 0 for u^2 >= U, and 0 for NaN.  The bias
-// 2^64 U comes from window_bias, hoisted out of the sample loops.
-constexpr float kMaskScale = 18446744073709551616.f;  // 2^64
-__device__ __forceinline__ float window_bias(float umax2) {
-  return kMaskScale * __int_as_float(__float_as_int(umax2) + 1);
-}
-__device__ __forceinline__ float window_mask(float sq, float bias) {
-  return __saturatef(fmaf(sq, -kMaskScale, bias));
-}
-
 // Bounded waits give up after this many nanoseconds of %globaltimer.
 constexpr unsigned long long WAIT_LIMIT_NS = 2000000000ull;
 
