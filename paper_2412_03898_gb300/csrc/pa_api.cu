@@ -283,10 +283,10 @@ constexpr int32_t kAdjChunkCandidates[] = {4, 8, 16, 32};
 constexpr size_t kQueueBytes = 256;
 
 // Ball splits of one scene in a batched forward: the plan's split count, else
-// one split per kMaxBallsPerSplit balls (narrower arrival bands per split), at
+// one split per kMaxBallsPerBatchedSplit balls (narrower arrival bands per split), at
 // most one per TMA stage of balls; balls per split a multiple of 4.
 void batched_splits(long long n, const int32_t *tiles, int nb_tile, int &n_splits, long long &bps) {
-  long long sp = tiles && tiles[3] > 0 ? tiles[3] : (n + pa::kMaxBallsPerSplit - 1) / pa::kMaxBallsPerSplit;
+  long long sp = tiles && tiles[3] > 0 ? tiles[3] : (n + pa::kMaxBallsPerBatchedSplit - 1) / pa::kMaxBallsPerBatchedSplit;
   sp = std::max(1LL, std::min(sp, (n + nb_tile - 1) / nb_tile));
   bps = (((n + sp - 1) / sp) + 3) & ~3LL;
   if (bps <= 0) bps = 4;

@@ -713,8 +713,8 @@ FwdPlan forward_plan(int S, int T, long long n, int F, int sms, int s_tile_o, in
   }
   // Smaller ball ranges have tighter bounding boxes, hence narrower arrival
   // bands and fewer culled chunks per CTA: at least one split per
-  // kMaxBallsPerSplit balls (on 1e6 balls x 50 frames x 1024 sensors:
-  // 1 split 4.01 s, 2 splits 3.48 s, 8 splits 3.20 s).
+  // kMaxBallsPerSplit balls (on 1e6 balls x 50 frames x 1024 sensors with
+  // earlier kernels: 1 split 4.01 s, 2 splits 3.48 s, 8 splits 3.20 s).
   if (splits_o <= 0) splits = std::max(splits, (n + kMaxBallsPerSplit - 1) / kMaxBallsPerSplit);
   splits = std::max(1LL, std::min(splits, max_splits));
   // balls per split: multiple of 4 so every TMA source stays 16-byte aligned

@@ -35,8 +35,16 @@ struct FwdArgs {
   unsigned *err;
 };
 
-// Default plans split larger ball sets (narrower arrival bands per split).
-constexpr long long kMaxBallsPerSplit = 131072;
+// Default plans split larger ball sets: a smaller ball range has a tighter
+// bounding box, hence a narrower arrival band at every sensor.  Single-scene
+// plans take at least one split per kMaxBallsPerSplit balls (one frame of 1e6
+// balls in a 60 mm phantom at 1024 sensors: 8 splits 41.8 ms, 16 splits
+// 38.3 ms, 32 splits 36.3 ms; 1e5 balls: unchanged at 4 or 16 splits); the
+// batched forward, whose partials of all scenes share one workspace, one per
+// kMaxBallsPerBatchedSplit (finer batched splits gave nothing on 16 uneven
+// scenes: 310 against 309 ms).
+constexpr long long kMaxBallsPerSplit = 32768;
+constexpr long long kMaxBallsPerBatchedSplit = 131072;
 
 // Batched (several scenes, one persistent launch).
 constexpr int kMaxScenes = 64;
