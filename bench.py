@@ -359,6 +359,7 @@ def run_ours(args):
     resid = torch.empty_like(traces)
     loss = torch.empty(1, dtype=torch.float64, device=dev)
     gstate = torch.empty_like(state)
+    aws = torch.empty(256, dtype=torch.uint8, device=dev)  # the adjoint's work-queue counter
     flush = torch.empty(512 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)
     stream = torch.cuda.current_stream()
 
@@ -372,7 +373,7 @@ def run_ours(args):
                          workspace=lws)
         if ev is not None:
             ev[2].record(stream)
-        pa.adjoint(geom, resid, state=state, n=n, out=gstate)
+        pa.adjoint(geom, resid, state=state, n=n, out=gstate, workspace=aws)
         if ev is not None:
             ev[3].record(stream)
 

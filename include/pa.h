@@ -71,6 +71,9 @@ extern "C" {
                                  p tau/(2R) on |tau| <= a), used for analytic tests */
 #define PA_PLAN_TUNE 8u       /* pa_plan_create only: time candidate plans on the caller's data */
 
+/* Scratch bytes of pa_adjoint's optional work-queue workspace. */
+#define PA_ADJOINT_WORKSPACE_BYTES 256u
+
 /* Acquisition geometry.  `sensors` is a device array [3][sensor_stride]
  * (x row, y row, z row) of sensor positions.  Constraints: n_sensors >= 1,
  * sensor_stride >= n_sensors, c > 0, fs > 0, t0 >= 0, n_samples >= 4 and a
@@ -160,7 +163,8 @@ PA_API const char *pa_status_string(int32_t status);
  * calls that recompute states per frame chunk (pa_forward_4d,
  * pa_adjoint_4d) and pa_measure_unit_rates, changed pa_forward_batched and
  * pa_adjoint_batched to take a plan in place of a tile array, and
- * pa_batched_workspace_size to take the scenes and the plan. */
+ * pa_batched_workspace_size to take the scenes and the plan.  2.01 gave
+ * pa_adjoint an optional work-queue workspace. */
 PA_API int32_t pa_version(void);
 
 /* Reads, returns in *out (host) and clears the device error word of the
@@ -239,10 +243,19 @@ PA_API int32_t pa_forward_plan_info(const pa_geom *geom, const pa_balls *balls, 
  *    stored) and the chain rule of Eq. 1-2 gives dL/d(canonical cloud) and
  *    dL/d(omega, theta, sigma), summed over frames.
  * Every per-ball gradient is written by exactly one warp: no atomics, and
- * deterministic.  Inactive balls (a <= 0 or p == 0) get zero state gradient. */
+ * deterministic.  Inactive balls (a <= 0 or p == 0) get zero state gradient.
+ * workspace: NULL, or device scratch of at least PA_ADJOINT_WORKSPACE_BYTES
+ * aligned to 256 bytes (else PA_ERR_WORKSPACE), which static mode uses as a
+ * work-queue counter: persistent warps then take (frame, ball) items from
+ * it, so warps that drew small windows take more items.  With NULL the items
+ * are dealt out in a fixed grid-stride order.  The results are identical
+ * either way (each item is computed whole by one warp); 4D mode ignores the
+ * workspace.  One workspace serves one call at a time: calls in flight on
+ * different streams need their own. */
 PA_API int32_t pa_adjoint(const pa_geom *geom, const pa_balls *balls, const pa_canon *canon,
                    const float *t_frames, int32_t n_frames, const float *trace_grad,
-                   const float *frame_scale, pa_grads *grads, uint32_t flags, void *stream);
+                   const float *frame_scale, pa_grads *grads, uint32_t flags, void *workspace,
+                   size_t workspace_bytes, void *stream);
 
 /* Scratch bytes the batched calls need for these scenes and this plan
  * (NULL: the heuristic): the work-queue counter (256 bytes, all that
@@ -333,8 +346,8 @@ PA_API int32_t pa_forward_4d(const pa_geom *geom, const pa_canon *canon, const f
                              float *traces, uint32_t flags, const pa_plan *plan, void *workspace,
                              size_t workspace_bytes, void *stream);
 
-/* Scratch bytes pa_adjoint_4d needs: one frame chunk of states and one of
- * state gradients, [K][5][stride] each. */
+/* Scratch bytes pa_adjoint_4d needs: a work-queue counter (256 bytes) and
+ * one frame chunk of states and one of state gradients, [K][5][stride] each. */
 PA_API size_t pa_adjoint_4d_workspace_size(const pa_geom *geom, const pa_canon *canon, int32_t n_frames,
                                            const pa_plan *plan);
 

@@ -265,10 +265,13 @@ def adjoint(geom: Geometry, trace_grad: torch.Tensor, state: Optional[torch.Tens
             n: Optional[int] = None, canon: Optional[torch.Tensor] = None, omega: Optional[torch.Tensor] = None,
             theta: Optional[torch.Tensor] = None, sigma: Optional[torch.Tensor] = None,
             t_frames: Optional[torch.Tensor] = None, frame_scale: Optional[torch.Tensor] = None,
-            accumulate: bool = False, out=None):
+            accumulate: bool = False, out=None, queue: bool = True, workspace: Optional[torch.Tensor] = None):
     """Adjoint of `forward`.  Static mode (state given): returns dL/dstate
     [F, 5, stride].  4D mode (canon, omega, theta, sigma, t_frames given):
-    returns (g_canon [5, stride], g_omega, g_theta, g_sigma [5, Nb, stride])."""
+    returns (g_canon [5, stride], g_omega, g_theta, g_sigma [5, Nb, stride]).
+    queue: static mode hands (frame, ball) items to warps from a work-queue
+    counter in `workspace` (256 bytes, allocated here when None); False
+    deals them out in grid-stride order.  The results are the same."""
     _check(trace_grad, "trace_grad")
     F = int(trace_grad.shape[0])
     if frame_scale is not None:
@@ -279,8 +282,14 @@ def adjoint(geom: Geometry, trace_grad: torch.Tensor, state: Optional[torch.Tens
         if out is None:
             out = torch.empty_like(state)
         grads = _lib.pa_grads(out.data_ptr(), None, None, None)
+        ws_ptr, ws_n = None, 0
+        if queue:
+            if workspace is None or workspace.numel() < _lib.PA_ADJOINT_WORKSPACE_BYTES:
+                workspace = torch.empty(_lib.PA_ADJOINT_WORKSPACE_BYTES, dtype=torch.uint8, device=state.device)
+            ws_ptr, ws_n = workspace.data_ptr(), workspace.numel() * workspace.element_size()
         _lib.check(_LIB.pa_adjoint(ctypes.byref(geom.struct()), ctypes.byref(bs), None, None, F,
-                                   trace_grad.data_ptr(), _ptr(frame_scale), ctypes.byref(grads), flags, _stream()),
+                                   trace_grad.data_ptr(), _ptr(frame_scale), ctypes.byref(grads), flags,
+                                   ws_ptr, ws_n, _stream()),
                    "pa_adjoint")
         return out
     cs, n = _canon_struct(canon, omega, theta, sigma, n)
@@ -289,7 +298,8 @@ def adjoint(geom: Geometry, trace_grad: torch.Tensor, state: Optional[torch.Tens
         out = (torch.empty_like(canon), torch.empty_like(omega), torch.empty_like(theta), torch.empty_like(sigma))
     grads = _lib.pa_grads(*[o.data_ptr() for o in out])
     _lib.check(_LIB.pa_adjoint(ctypes.byref(geom.struct()), None, ctypes.byref(cs), t_frames.data_ptr(), F,
-                               trace_grad.data_ptr(), _ptr(frame_scale), ctypes.byref(grads), flags, _stream()),
+                               trace_grad.data_ptr(), _ptr(frame_scale), ctypes.byref(grads), flags, None, 0,
+                               _stream()),
                "pa_adjoint")
     return out
 

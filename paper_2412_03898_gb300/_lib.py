@@ -21,6 +21,7 @@ PA_ACCUMULATE = 1
 PA_SSIM_MINMAX = 4
 PA_PROFILE_UNIFORM = 2
 PA_PLAN_TUNE = 8
+PA_ADJOINT_WORKSPACE_BYTES = 256
 
 c_float_p = ctypes.c_void_p  # device pointers travel as void*
 
@@ -92,7 +93,7 @@ def load() -> ctypes.CDLL:
         "pa_forward": (i32, [G, B, i32, P, u32, P, sz, P]),
         "pa_forward_ex": (i32, [G, B, i32, P, u32, I32P, P, sz, P]),
         "pa_forward_plan_info": (i32, [G, B, i32, I32P, I32P]),
-        "pa_adjoint": (i32, [G, B, C, P, i32, P, P, GR, u32, P]),
+        "pa_adjoint": (i32, [G, B, C, P, i32, P, P, GR, u32, P, sz, P]),
         "pa_batched_workspace_size": (sz, [ctypes.POINTER(pa_scene), i32, P]),
         "pa_forward_batched": (i32, [ctypes.POINTER(pa_scene), i32, u32, P, P, sz, P]),
         "pa_adjoint_batched": (i32, [ctypes.POINTER(pa_scene), i32, u32, P, P, sz, P]),

@@ -244,8 +244,7 @@ __global__ void __launch_bounds__(32 * kAdjWarps, 4) k_adjoint_static(const AdjA
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   float4 *rec = recs + warp * 96;
   bool dom = false;
-  for (long long item = (long long)blockIdx.x * kAdjWarps + warp; item < A.n_items;
-       item += (long long)gridDim.x * kAdjWarps) {
+  auto body = [&](long long item) {
     const int f = (int)(item / A.n);
     const long long b = item - (long long)f * A.n;
     const float *st = A.state + (long long)f * 5 * A.stride;
@@ -267,6 +266,24 @@ __global__ void __launch_bounds__(32 * kAdjWarps, 4) k_adjoint_static(const AdjA
       float *dst = A.g_state + (long long)f * 5 * A.stride + lane * A.stride + b;
       *dst = (A.flags & PA_ACCUMULATE) ? *dst + gv : gv;
     }
+  };
+  if (A.queue != nullptr) {
+    // Persistent warps take A.queue_chunk items at a time from the counter,
+    // so a warp that drew cheap balls (small windows) takes more of them and
+    // no block waits for its slowest warp.  Each item is still computed whole
+    // by one warp: the results do not depend on the assignment.
+    while (true) {
+      unsigned long long base = 0;
+      if (lane == 0) base = atomicAdd(A.queue, (unsigned long long)A.queue_chunk);
+      base = __shfl_sync(FULL, base, 0);
+      if ((long long)base >= A.n_items) break;
+      const long long end = min((long long)base + A.queue_chunk, A.n_items);
+      for (long long item = (long long)base; item < end; ++item) body(item);
+    }
+  } else {
+    for (long long item = (long long)blockIdx.x * kAdjWarps + warp; item < A.n_items;
+         item += (long long)gridDim.x * kAdjWarps)
+      body(item);
   }
   if (dom) set_error(A.err, PA_ERR_DOMAIN);
 }
@@ -447,9 +464,26 @@ cudaError_t launch_gridstride(K kern, const AdjArgs &a, size_t smem, int sms, cu
 
 }  // namespace
 
-cudaError_t launch_adjoint_static(const AdjArgs &a, int sms, cudaStream_t st) {
-  if (a.n_items == 0) return cudaSuccess;
-  return launch_gridstride(k_adjoint_static, a, adj_static_smem(a.q.S), sms, st);
+cudaError_t launch_adjoint_static(const AdjArgs &a0, int sms, cudaStream_t st) {
+  if (a0.n_items == 0) return cudaSuccess;
+  const size_t smem = adj_static_smem(a0.q.S);
+  if (a0.queue == nullptr) return launch_gridstride(k_adjoint_static, a0, smem, sms, st);
+  // work queue: one wave of persistent blocks
+  AdjArgs a = a0;
+  cudaError_t e = cudaFuncSetAttribute(k_adjoint_static, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  if (e != cudaSuccess) return e;
+  int occ = 0;
+  e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_adjoint_static, 32 * kAdjWarps, smem);
+  if (e != cudaSuccess) return e;
+  if (occ < 1) return cudaErrorInvalidConfiguration;
+  const long long warps = (long long)sms * occ * kAdjWarps;
+  // items per grab: small enough that the tail is short (about 1/32 of a
+  // warp's share), at least 2 and at most 16 to bound the atomics
+  a.queue_chunk = (int)std::max(2LL, std::min(16LL, a.n_items / (warps * 32)));
+  e = cudaMemsetAsync(a.queue, 0, sizeof(unsigned long long), st);
+  if (e != cudaSuccess) return e;
+  k_adjoint_static<<<(unsigned)(sms * occ), 32 * kAdjWarps, smem, st>>>(a);
+  return cudaGetLastError();
 }
 
 cudaError_t launch_adjoint_batched(const BatchAdjArgs &a, int sms, cudaStream_t st) {

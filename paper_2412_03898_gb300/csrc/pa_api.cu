@@ -279,8 +279,10 @@ constexpr int32_t kTileCandidates[][5] = {
 constexpr int kNumTileCandidates = sizeof(kTileCandidates) / sizeof(kTileCandidates[0]);
 constexpr int32_t kAdjChunkCandidates[] = {4, 8, 16, 32};
 
-// Bytes at the start of a batched call's workspace: its work-queue counter.
+// Bytes at the start of a batched or pa_adjoint_4d workspace: its work-queue
+// counter.
 constexpr size_t kQueueBytes = 256;
+static_assert(kQueueBytes == PA_ADJOINT_WORKSPACE_BYTES, "one queue slot layout");
 
 // Ball splits of one scene in a batched forward: the plan's split count, else
 // one split per kMaxBallsPerBatchedSplit balls (narrower arrival bands per split), at
@@ -351,7 +353,7 @@ const char *pa_status_string(int32_t status) {
   }
 }
 
-int32_t pa_version(void) { return 200; }
+int32_t pa_version(void) { return 201; }
 
 int32_t pa_device_error(void *stream, int32_t *out) {
   if (out == nullptr) return PA_ERR_INVALID_ARG;
@@ -446,10 +448,12 @@ int32_t pa_forward_plan_info(const pa_geom *geom, const pa_balls *balls, int32_t
 
 int32_t pa_adjoint(const pa_geom *geom, const pa_balls *balls, const pa_canon *canon, const float *t_frames,
                    int32_t n_frames, const float *trace_grad, const float *frame_scale, pa_grads *grads,
-                   uint32_t flags, void *stream) {
+                   uint32_t flags, void *workspace, size_t workspace_bytes, void *stream) {
   int rc = check_geom(geom);
   if (rc) return rc;
   if (n_frames < 0 || grads == nullptr || (flags & ~PA_ACCUMULATE) != 0) return PA_ERR_INVALID_ARG;
+  if (workspace != nullptr && (workspace_bytes < PA_ADJOINT_WORKSPACE_BYTES || !aligned(workspace, 256)))
+    return PA_ERR_WORKSPACE;
   const bool four_d = canon != nullptr;
   if ((balls != nullptr) == four_d) return PA_ERR_INVALID_ARG;  // exactly one mode
   if (four_d) {
@@ -507,6 +511,7 @@ int32_t pa_adjoint(const pa_geom *geom, const pa_balls *balls, const pa_canon *c
   a.state = balls->state;
   a.stride = balls->stride;
   a.n_items = (long long)n_frames * n;
+  a.queue = static_cast<unsigned long long *>(workspace);
   const size_t smem = sizeof(float4) * 8 * 96 + sizeof(float) * 3 * (size_t)geom->n_sensors;
   if ((long long)smem > d->max_smem) return PA_ERR_INVALID_ARG;
   return cuda_status(pa::launch_adjoint_static(a, d->sms, st));
@@ -1090,7 +1095,7 @@ size_t pa_adjoint_4d_workspace_size(const pa_geom *geom, const pa_canon *canon, 
                                     const pa_plan *plan) {
   if (check_geom(geom) || check_canon(canon) || n_frames <= 0 || canon->n == 0) return 0;
   const int K = frames_per_chunk(plan, canon->n_basis, n_frames);
-  return 2 * chunk_state_bytes(canon, K);
+  return kQueueBytes + 2 * chunk_state_bytes(canon, K);
 }
 
 int32_t pa_adjoint_4d(const pa_geom *geom, const pa_canon *canon, const float *t_frames, int32_t n_frames,
@@ -1120,9 +1125,11 @@ int32_t pa_adjoint_4d(const pa_geom *geom, const pa_canon *canon, const float *t
   }
   const int K = frames_per_chunk(plan, canon->n_basis, n_frames);
   const size_t sbytes = chunk_state_bytes(canon, K);
-  if (workspace == nullptr || workspace_bytes < 2 * sbytes || !aligned(workspace, 256)) return PA_ERR_WORKSPACE;
-  float *states = static_cast<float *>(workspace);
-  float *gstates = reinterpret_cast<float *>(static_cast<char *>(workspace) + sbytes);
+  if (workspace == nullptr || workspace_bytes < kQueueBytes + 2 * sbytes || !aligned(workspace, 256))
+    return PA_ERR_WORKSPACE;
+  auto *queue = static_cast<unsigned long long *>(workspace);
+  float *states = reinterpret_cast<float *>(static_cast<char *>(workspace) + kQueueBytes);
+  float *gstates = reinterpret_cast<float *>(static_cast<char *>(workspace) + kQueueBytes + sbytes);
   const size_t per_frame = (size_t)geom->n_sensors * geom->n_samples;
   for (int f0 = 0; f0 < n_frames; f0 += K) {
     const int k = std::min(K, n_frames - f0);
@@ -1142,6 +1149,7 @@ int32_t pa_adjoint_4d(const pa_geom *geom, const pa_canon *canon, const float *t
     a.flags = 0;
     a.err = d->err;
     a.n_items = (long long)k * canon->n;
+    a.queue = queue;
     rc = cuda_status(pa::launch_adjoint_static(a, d->sms, st));
     if (rc) return rc;
     rc = cuda_status(pa::launch_deform_backward(canon->canon, canon->omega, canon->theta, canon->sigma, canon->n,

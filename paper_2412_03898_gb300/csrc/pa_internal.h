@@ -107,6 +107,8 @@ struct AdjArgs {
   unsigned flags;
   unsigned *err;
   long long n_items;
+  unsigned long long *queue;  // static mode: work-queue counter in a workspace, or nullptr (grid-stride loop)
+  int queue_chunk;            // items per grab (set by the launcher)
 };
 
 // Plan selection (tile sizes, splits); `override` entries > 0 replace the

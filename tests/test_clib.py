@@ -179,7 +179,25 @@ def test_4d_calls_and_probe_reject_bad_args_on_host(lib):
                              None, fake, 4096, None) == E
     assert lib.pa_forward_4d_workspace_size(ctypes.byref(g), ctypes.byref(bad_nb), 2, None) == 0
     assert lib.pa_adjoint_4d_workspace_size(None, ctypes.byref(good), 2, None) == 0
+    # work-queue counter (256) + one frame of states and one of gradients
+    # (5 x stride 4 floats, rounded up to 256 bytes each)
+    assert lib.pa_adjoint_4d_workspace_size(ctypes.byref(g), ctypes.byref(good), 2, None) == 256 + 2 * 256
     assert lib.pa_measure_unit_rates(None, None) == E
+
+
+def test_adjoint_workspace_checked_on_host(lib):
+    from paper_2412_03898_gb300 import _lib
+    W = _lib.PA_ERR_WORKSPACE
+    P = ctypes.c_void_p
+    fake = P(256)  # never dereferenced: the workspace check fails first
+    g = _lib.pa_geom(16, 4, 4, 1.5, 40.0, 0.0, 64, 5.0)
+    b = _lib.pa_balls(16, 4, 4)
+    gr = _lib.pa_grads(16, None, None, None)
+    args = (ctypes.byref(g), ctypes.byref(b), None, None, 1, fake, None, ctypes.byref(gr), 0)
+    assert lib.pa_adjoint(*args, P(256 + 16), 256, None) == W  # not 256-byte aligned
+    assert lib.pa_adjoint(*args, fake, 128, None) == W  # smaller than PA_ADJOINT_WORKSPACE_BYTES
+    hdr = open(os.path.join(ROOT, "include", "pa.h")).read()
+    assert int(re.search(r"#define PA_ADJOINT_WORKSPACE_BYTES (\d+)u", hdr).group(1)) == _lib.PA_ADJOINT_WORKSPACE_BYTES
 
 
 def test_noalloc_loss_rejects_problems_beyond_its_scratch_on_host(lib):

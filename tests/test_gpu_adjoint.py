@@ -34,6 +34,8 @@ def test_adjoint_static_parity(pa, seed, n, ns, T, F):
     geom = geometry(sc)
     got = pa.adjoint(geom, torch.from_numpy(g).cuda(), state=dev_pad(states), n=n)
     pa.device_error()
+    fixed = pa.adjoint(geom, torch.from_numpy(g).cuda(), state=dev_pad(states), n=n, queue=False)
+    assert torch.equal(got[..., :n], fixed[..., :n])  # work-queue and grid-stride schedules
     want = oracle.adjoint_state(states, sc.sensors, *_geom_args(sc), g)
     got = got[:, :, :n].cpu().numpy()
     for ch, name in enumerate("xyzap"):

@@ -11,7 +11,9 @@ checks only sampled outputs at these sizes):
   ball gradient of the adjoint, so a tile-seam or window-edge error in either
   kernel breaks it;
 - doubling every p doubles every trace sample bitwise (power-of-two scaling
-  is exact through the whole path).
+  is exact through the whole path);
+- the adjoint's work-queue and grid-stride schedules give bitwise the same
+  gradients.
 
 Workloads: static-100k (all 100k balls, 576 sensors x 4096 samples) and the
 canonical frame of the 1M-ball workload (1024 sensors x 4096 samples)."""
@@ -56,5 +58,8 @@ def test_full_size_superposition_inner_product_and_scaling(cfg):
     lhs = float((y.double() * g.double()).sum())
     gs = pa.adjoint(geom, g, state=st, n=n)
     pa.device_error()
+    # the work-queue schedule (default) and the grid-stride one compute each
+    # (frame, ball) item whole in one warp: bitwise the same gradients
+    assert torch.equal(gs[..., :n], pa.adjoint(geom, g, state=st, n=n, queue=False)[..., :n])
     rhs = float((st[0, 4, :n].double() * gs[0, 4, :n].double()).sum())
     assert abs(lhs - rhs) <= 1e-5 * abs(lhs), (lhs, rhs)
