@@ -7,15 +7,15 @@
 //  - One warp owns one ball (static mode: one (frame, ball) item) and loops
 //    over all sensors.  The 32 lanes compute the window, phase and gradient
 //    factors of 32 (ball, sensor) pairs in parallel and publish them,
-//    compacted, in shared memory; the warp then walks sixteen pairs at a
-//    time, one per 2-lane sub-warp, each lane on eight consecutive samples
-//    per step (one 256-bit residual load from L2 when the rows are 32-byte
-//    aligned, else four samples per float4 load; packed FP32x2 arithmetic;
-//    next step's load in flight), accumulating per lane
+//    compacted, in shared memory; then each lane walks one pair's window,
+//    eight consecutive samples per step (one 256-bit residual load from L2
+//    when the rows are 32-byte aligned, else four samples per float4 load;
+//    packed FP32x2 arithmetic; the next step's load in flight, unpredicated
+//    and double-buffered on the steps inside every lane's window),
+//    accumulating
 //        S1 = sum g E u,  S3 = sum g E u^3,  SR = sum g E (1 - tau^2/a^2)
-//    which one shuffle between the sub-warp's two lanes turns into the
-//    pair's sums; the sub-warp's first lane folds them with the pair's
-//    factors into its gradient accumulators.
+//    and folding them with the pair's factors into its gradient
+//    accumulators.
 //  - A warp-shuffle reduction over lanes (i.e. over sensors and samples) at
 //    the end of the ball gives dL/d(x, y, z, a, p); one lane writes it.
 //  - 4D mode recomputes the deformed state of the ball per frame in registers
@@ -81,62 +81,58 @@ __device__ __forceinline__ void ball_frame_grad(const Acq &q, const float *gfram
         rec[3 * pos + 2] = r2;
       }
       __syncwarp();
-      // Sixteen pairs at a time, one per 2-lane sub-warp: each sub-warp walks
-      // its pair's whole window, each lane eight (or four) consecutive
-      // samples per step (one 256-bit or float4 residual load, packed FP32x2
-      // halves), the next step's load issued before the current step's
-      // arithmetic.  All pairs belong to one ball, so their windows have
-      // nearly the same length and the sub-warps finish together.  Samples
-      // of the aligned loads outside the window get weight 0 from the window
-      // test (u^2 <= (kappa K_S)^2, the forward's own test).
-      const int sub = lane >> 1, sl = lane & 1;
-      const float2 negk = make_float2(-K_2LN2, -K_2LN2), one = make_float2(1.f, 1.f);
-      for (int g0 = 0; g0 < nv; g0 += 16) {
-        const int i = g0 + sub;
+      // One pair per lane: each lane walks its own pair's whole window, eight
+      // (or four) consecutive samples per step (one 256-bit or float4
+      // residual load, predicated, issued one step ahead; packed FP32x2
+      // halves).  All pairs belong to one ball, so their windows have nearly
+      // the same length and the lanes finish together.  Samples of the
+      // aligned loads outside the window get weight 0 from the window test
+      // (u^2 <= (kappa K_S)^2, the forward's own test).
+      const float2 one = make_float2(1.f, 1.f);
+      const float4 zero4 = make_float4(0.f, 0.f, 0.f, 0.f);
+      for (int g0 = 0; g0 < nv; g0 += 32) {
+        const int i = g0 + lane;
         const bool act = i < nv;
         const int ii = act ? i : 0;
         const float4 a0 = rec[3 * ii + 0], a2 = rec[3 * ii + 2];
         const int klo = __float_as_int(a2.y);
         const int khi = act ? klo + __float_as_int(a2.z) - 1 : -1;
-        // float4-aligned start: rows start 16-byte aligned (T % 4 == 0), and
-        // a float4 starting at k <= khi <= T - 1 ends at k + 3 <= T - 1
-        const int ka = klo & ~3;
-        const float4 *row = reinterpret_cast<const float4 *>(gframe + (long long)__float_as_int(a2.w) * T);
-        const int nit = act ? ((khi - ka) >> 3) + 1 : 0;
-        const int nmax = wide ? 0 : __reduce_max_sync(FULL, nit);
-        int kk = ka + 4 * sl;
+        const float *rowf = gframe + (long long)__float_as_int(a2.w) * T;
         const float du = a0.y;
-        float2 ua, ub;  // u at kk, kk + 1 and kk + 2, kk + 3
-        ua.x = fmaf((float)(kk - klo), -du, a0.x);
-        ua.y = ua.x - du;
-        ub.x = fmaf(-2.f, du, ua.x);
-        ub.y = fmaf(-3.f, du, ua.x);
-        const float2 nd2 = make_float2(-8.f * du, -8.f * du);
         float2 S1 = make_float2(0.f, 0.f), S3 = S1, SR = S1;
+        // nsq = -u^2 (the exponent of E = 2^(-u^2)) from one packed multiply
+        // by -u; S3 accumulates -sum g E u^3 and is negated once per pair
+        const float2 pk2 = make_float2(K_2LN2, K_2LN2);
         auto half = [&](const float2 u2, const float2 g2) {
-          const float2 sq = __fmul2_rn(u2, u2);                                      // u^2
+          const float2 nsq = __fmul2_rn(u2, make_float2(-u2.x, -u2.y));             // -u^2
           // exp(-tau^2/(2a^2)) inside the window, 0 outside it (compare and
           // select on the ALU pipe, which has room; the FMA pipe has not)
-          const float2 E = make_float2(sq.x <= umax2 ? ex2(-sq.x) : 0.f, sq.y <= umax2 ? ex2(-sq.y) : 0.f);
+          const float2 E = make_float2(nsq.x >= -umax2 ? ex2(nsq.x) : 0.f, nsq.y >= -umax2 ? ex2(nsq.y) : 0.f);
           const float2 ge = __fmul2_rn(g2, E);
           const float2 gu = __fmul2_rn(ge, u2);
           S1 = __fadd2_rn(S1, gu);                                                   // sum g E u
-          S3 = __ffma2_rn(gu, sq, S3);                                               // sum g E u^3
-          SR = __ffma2_rn(ge, __ffma2_rn(sq, negk, one), SR);                        // sum g E (1 - tau^2/a^2)
+          S3 = __ffma2_rn(gu, nsq, S3);                                              // -sum g E u^3
+          SR = __ffma2_rn(ge, __ffma2_rn(nsq, pk2, one), SR);                        // sum g E (1 - tau^2/a^2)
         };
-        const float4 zero4 = make_float4(0.f, 0.f, 0.f, 0.f);
+        auto halfu = [&](const float2 u2, const float2 g2) {  // `half` inside the window (no test)
+          const float2 nsq = __fmul2_rn(u2, make_float2(-u2.x, -u2.y));
+          const float2 E = make_float2(ex2(nsq.x), ex2(nsq.y));
+          const float2 ge = __fmul2_rn(g2, E);
+          const float2 gu = __fmul2_rn(ge, u2);
+          S1 = __fadd2_rn(S1, gu);
+          S3 = __ffma2_rn(gu, nsq, S3);
+          SR = __ffma2_rn(ge, __ffma2_rn(nsq, pk2, one), SR);
+        };
         if (wide) {
-          // 256-bit loads: each lane eight consecutive samples per 16-sample
-          // step, from a 32-byte aligned start (rows are 32-byte aligned when
-          // T % 8 == 0; a load starting at k <= khi <= T - 1 with k % 8 == 0
-          // ends at k + 7 <= T - 1)
-          const int ka8 = klo & ~7;
-          const float *rowf = gframe + (long long)__float_as_int(a2.w) * T;
-          const int nit8 = act ? ((khi - ka8) >> 4) + 1 : 0;
-          const int nmax8 = __reduce_max_sync(FULL, nit8);
-          int k8 = ka8 + 8 * sl;
-          float2 uc, ud;  // u at k8 + 4, k8 + 5 and k8 + 6, k8 + 7
-          ua.x = fmaf((float)(k8 - klo), -du, a0.x);
+          // 256-bit loads from a 32-byte aligned start (rows are 32-byte
+          // aligned when T % 8 == 0; a load starting at k <= khi <= T - 1
+          // with k % 8 == 0 ends at k + 7 <= T - 1)
+          const int ka = klo & ~7;
+          const int nit = act ? ((khi - ka) >> 3) + 1 : 0;
+          const int nmax = __reduce_max_sync(FULL, nit);
+          int k = ka;
+          float2 ua, ub, uc, ud;  // u at k, k + 1 | k + 2, k + 3 | k + 4, k + 5 | k + 6, k + 7
+          ua.x = fmaf((float)(k - klo), -du, a0.x);
           ua.y = ua.x - du;
           ub.x = fmaf(-2.f, du, ua.x);
           ub.y = fmaf(-3.f, du, ua.x);
@@ -144,69 +140,96 @@ __device__ __forceinline__ void ball_frame_grad(const Acq &q, const float *gfram
           uc.y = fmaf(-5.f, du, ua.x);
           ud.x = fmaf(-6.f, du, ua.x);
           ud.y = fmaf(-7.f, du, ua.x);
-          const float2 nd16 = make_float2(-16.f * du, -16.f * du);
-          float4 c0 = zero4, c1 = zero4;
-          if (k8 <= khi) ldg8(rowf + k8, c0, c1);
-          auto halfu = [&](const float2 u2, const float2 g2) {  // `half` without the window mask
-            const float2 sq = __fmul2_rn(u2, u2);
-            const float2 E = make_float2(ex2(-sq.x), ex2(-sq.y));
-            const float2 ge = __fmul2_rn(g2, E);
-            const float2 gu = __fmul2_rn(ge, u2);
-            S1 = __fadd2_rn(S1, gu);
-            S3 = __ffma2_rn(gu, sq, S3);
-            SR = __ffma2_rn(ge, __ffma2_rn(sq, negk, one), SR);
-          };
-          auto step = [&](auto masked) {
-            float4 n0 = zero4, n1 = zero4;
-            if (k8 + 16 <= khi) ldg8(rowf + k8 + 16, n0, n1);
+          const float2 nd8 = make_float2(-8.f * du, -8.f * du);
+          const float *pk = rowf + k;
+          auto eval = [&](auto masked, const float4 &x0, const float4 &x1) {
             if (decltype(masked)::value) {
-              half(ua, make_float2(c0.x, c0.y));
-              half(ub, make_float2(c0.z, c0.w));
-              half(uc, make_float2(c1.x, c1.y));
-              half(ud, make_float2(c1.z, c1.w));
+              half(ua, make_float2(x0.x, x0.y));
+              half(ub, make_float2(x0.z, x0.w));
+              half(uc, make_float2(x1.x, x1.y));
+              half(ud, make_float2(x1.z, x1.w));
             } else {
-              halfu(ua, make_float2(c0.x, c0.y));
-              halfu(ub, make_float2(c0.z, c0.w));
-              halfu(uc, make_float2(c1.x, c1.y));
-              halfu(ud, make_float2(c1.z, c1.w));
+              halfu(ua, make_float2(x0.x, x0.y));
+              halfu(ub, make_float2(x0.z, x0.w));
+              halfu(uc, make_float2(x1.x, x1.y));
+              halfu(ud, make_float2(x1.z, x1.w));
             }
-            ua = __fadd2_rn(ua, nd16);
-            ub = __fadd2_rn(ub, nd16);
-            uc = __fadd2_rn(uc, nd16);
-            ud = __fadd2_rn(ud, nd16);
+            ua = __fadd2_rn(ua, nd8);
+            ub = __fadd2_rn(ub, nd8);
+            uc = __fadd2_rn(uc, nd8);
+            ud = __fadd2_rn(ud, nd8);
+            pk += 8;
+            k += 8;
+          };
+          // A step with the window test, its successor's load predicated on
+          // lying in the walk (zeros past it).
+          auto edge_step = [&](float4 &c0, float4 &c1) {
+            float4 n0 = zero4, n1 = zero4;
+            ldg8_if(pk + 8, k + 8 <= khi, n0, n1);
+            eval(std::true_type{}, c0, c1);
             c0 = n0;
             c1 = n1;
-            k8 += 16;
           };
           // Only a walk's first and last step can hold samples outside its
-          // window: steps 1 .. nit8 - 2 lie strictly inside it (the mask is
-          // exactly 1 there).  Steps inside every active sub-warp's walk skip
-          // the mask; the split is warp-uniform.
-          const int mn = __reduce_min_sync(FULL, act ? nit8 : 0x7fffffff);
+          // window: steps 1 .. nit - 2 lie strictly inside it (the test is
+          // exactly 1 there).  Steps 1 .. e1 - 1, inside every active lane's
+          // walk, skip the test, and their successors' loads (steps up to
+          // e1 <= mn - 1 <= nit - 1) lie inside every active lane's walk, so
+          // they are issued unpredicated (an inactive lane reads pair 0's row
+          // inside pair 0's walk and discards its sums).  The split is
+          // warp-uniform.
+          const int mn = __reduce_min_sync(FULL, act ? nit : 0x7fffffff);
+          const int e1 = min(mn - 1, nmax);
+          float4 c0 = zero4, c1 = zero4;
+          ldg8_if(pk, k <= khi, c0, c1);
           int it = 0;
-          if (nmax8 > 0) {
-            step(std::true_type{});
+          if (nmax > 0) {
+            edge_step(c0, c1);
             ++it;
           }
-          const int e1 = min(mn - 1, nmax8);
-          for (; it < e1; ++it) step(std::false_type{});
-          for (; it < nmax8; ++it) step(std::true_type{});
+          for (; it + 1 < e1; it += 2) {  // two interior steps, loads double-buffered
+            float4 n0, n1;
+            ldg8(pk + 8, n0, n1);
+            eval(std::false_type{}, c0, c1);
+            ldg8(pk + 8, c0, c1);
+            eval(std::false_type{}, n0, n1);
+          }
+          if (it < e1) {
+            float4 n0, n1;
+            ldg8(pk + 8, n0, n1);
+            eval(std::false_type{}, c0, c1);
+            c0 = n0;
+            c1 = n1;
+            ++it;
+          }
+          for (; it < nmax; ++it) edge_step(c0, c1);
         } else {
-          float4 gcur = kk <= khi ? __ldg(row + (kk >> 2)) : zero4;
-          for (int it = 0; it < nmax; ++it, kk += 8) {
-            const float4 gnext = kk + 8 <= khi ? __ldg(row + ((kk + 8) >> 2)) : zero4;
+          // float4 loads: rows start 16-byte aligned (T % 4 == 0), and a
+          // float4 starting at k <= khi <= T - 1 with k % 4 == 0 ends at
+          // k + 3 <= T - 1
+          const int ka = klo & ~3;
+          const int nit = act ? ((khi - ka) >> 2) + 1 : 0;
+          const int nmax = __reduce_max_sync(FULL, nit);
+          int k = ka;
+          float2 ua, ub;  // u at k, k + 1 | k + 2, k + 3
+          ua.x = fmaf((float)(k - klo), -du, a0.x);
+          ua.y = ua.x - du;
+          ub.x = fmaf(-2.f, du, ua.x);
+          ub.y = fmaf(-3.f, du, ua.x);
+          const float2 nd4 = make_float2(-4.f * du, -4.f * du);
+          const float4 *row = reinterpret_cast<const float4 *>(rowf);
+          float4 gcur = k <= khi ? __ldg(row + (k >> 2)) : zero4;
+          for (int it = 0; it < nmax; ++it, k += 4) {
+            const float4 gnext = k + 4 <= khi ? __ldg(row + ((k + 4) >> 2)) : zero4;
             half(ua, make_float2(gcur.x, gcur.y));
             half(ub, make_float2(gcur.z, gcur.w));
-            ua = __fadd2_rn(ua, nd2);
-            ub = __fadd2_rn(ub, nd2);
+            ua = __fadd2_rn(ua, nd4);
+            ub = __fadd2_rn(ub, nd4);
             gcur = gnext;
           }
         }
-        float s1 = S1.x + S1.y, s3 = S3.x + S3.y, sr = SR.x + SR.y;
-        s1 += __shfl_xor_sync(FULL, s1, 1);
-        s3 += __shfl_xor_sync(FULL, s3, 1);
-        sr += __shfl_xor_sync(FULL, sr, 1);
-        if (sl == 0 && act) {
+        const float s1 = S1.x + S1.y, s3 = -(S3.x + S3.y), sr = SR.x + SR.y;
+        if (act) {
           const float4 a1 = rec[3 * ii + 1];
           gp = fmaf(s1, a0.z, gp);
           ga = fmaf(s3, -a0.w, ga);  // record holds -A/K_S^3 for sum g E u (-u^2)

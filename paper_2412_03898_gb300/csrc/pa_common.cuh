@@ -85,9 +85,18 @@ __device__ __forceinline__ float ex2(float x) {
 // Eight consecutive floats from read-only global memory in one 256-bit load
 // (PTX ld.global.nc.v8.f32, sm_100 and later); p must be 32-byte aligned.
 __device__ __forceinline__ void ldg8(const float *p, float4 &lo, float4 &hi) {
-  asm volatile("ld.global.nc.v8.f32 {%0, %1, %2, %3, %4, %5, %6, %7}, [%8];"
+  asm("ld.global.nc.v8.f32 {%0, %1, %2, %3, %4, %5, %6, %7}, [%8];"
                : "=f"(lo.x), "=f"(lo.y), "=f"(lo.z), "=f"(lo.w), "=f"(hi.x), "=f"(hi.y), "=f"(hi.z), "=f"(hi.w)
                : "l"(p));
+}
+
+// ldg8 when `pred` holds, else lo and hi keep their values (predicated load,
+// no branch).
+__device__ __forceinline__ void ldg8_if(const float *p, bool pred, float4 &lo, float4 &hi) {
+  asm("{\n\t.reg .pred q;\n\tsetp.ne.b32 q, %9, 0;\n\t"
+      "@q ld.global.nc.v8.f32 {%0, %1, %2, %3, %4, %5, %6, %7}, [%8];\n\t}"
+      : "+f"(lo.x), "+f"(lo.y), "+f"(lo.z), "+f"(lo.w), "+f"(hi.x), "+f"(hi.y), "+f"(hi.z), "+f"(hi.w)
+      : "l"(p), "r"((int)pred));
 }
 
 __device__ __forceinline__ unsigned long long global_ns() {
