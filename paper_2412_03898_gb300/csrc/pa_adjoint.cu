@@ -5,9 +5,9 @@
 //
 // Design (GB300, sm_103a): ball-major, no atomics.
 //  - One warp owns one ball (static mode: one (frame, ball) item) and loops
-//    over all sensors.  The 32 lanes compute the window, phase and gradient
-//    factors of 32 (ball, sensor) pairs in parallel and publish them,
-//    compacted, in shared memory; then each lane walks one pair's window,
+//    over all sensors.  The 32 lanes compute the windows and phases of 32
+//    (ball, sensor) pairs in parallel and compact the valid ones to the
+//    front lanes with register shuffles; then each lane walks one pair's window,
 //    eight consecutive samples per step (one 256-bit residual load from L2
 //    when the rows are 32-byte aligned, else four samples per float4 load;
 //    packed FP32x2 arithmetic; the next step's load in flight, unpredicated
@@ -43,10 +43,20 @@ constexpr int kAdjWarps = 8;
 // samples.  Returns the totals (identical in every lane).
 // Sensor coordinates are read from sens[c * sstr + s] (shared memory, or the
 // global sensor array of a batched scene).
+// Bit position of the (i+1)-th set bit of m (0 <= i < popc(m)), by binary
+// search over prefix counts.
+__device__ __forceinline__ int nth_set_bit(unsigned m, int i) {
+  int lo = 0;
+#pragma unroll
+  for (int w = 16; w > 0; w >>= 1)
+    if (__popc(m & ((1u << (lo + w)) - 1u)) <= i) lo += w;
+  return lo;
+}
+
 template <bool ALLOW_WIDE>
 __device__ __forceinline__ void ball_frame_grad(const Acq &q, const float *gframe, const float *sens, int sstr,
-                                                float4 *rec, int lane, float bx, float by, float bz, float a,
-                                                float p, float out[5], bool &dom) {
+                                                int lane, float bx, float by, float bz, float a, float p,
+                                                float out[5], bool &dom) {
   const int S = q.S, T = q.T;
   const float umax2 = (q.kappa * K_S) * (q.kappa * K_S);  // the forward's window test u^2 <= umax2
   // 256-bit residual loads need 32-byte aligned rows
@@ -54,51 +64,48 @@ __device__ __forceinline__ void ball_frame_grad(const Acq &q, const float *gfram
   float gx = 0.f, gy = 0.f, gz = 0.f, ga = 0.f, gp = 0.f;
   if (a > 0.f && p != 0.f) {
     for (int s0 = 0; s0 < S; s0 += 32) {
-      const int s = s0 + lane;
-      int W = 0;
-      float4 r0 = make_float4(0.f, 0.f, 0.f, 0.f), r1 = r0, r2 = r0;
-      if (s < S) {
+      int W = 0, klo = 0;
+      float u0 = 0.f, du = 0.f, R = 0.f;
+      if (s0 + lane < S) {
+        const int s = s0 + lane;
         const float sx = sens[s], sy = sens[sstr + s], sz = sens[2 * sstr + s];
         const PairWin w = pair_window<false>(q, bx, by, bz, a, p, sx, sy, sz, 0, T - 1);
         dom |= w.domain_err;
         W = w.W;
-        if (W > 0) {
-          const float invR = __fdividef(1.f, w.R);
-          const float amp = 0.5f * p * invR;        // A = p/(2R)
-          const float aK = a * (1.f / K_S);         // 1/s
-          r0 = make_float4(w.u0, w.du, 0.5f * invR * aK, -amp * (1.f / (K_S * K_S * K_S)));
-          r1 = make_float4(-amp * invR * aK, amp, (bx - sx) * invR, (by - sy) * invR);
-          r2 = make_float4((bz - sz) * invR, __int_as_float(w.klo), __int_as_float(W), __int_as_float(s));
-        }
+        klo = w.klo;
+        u0 = w.u0;
+        du = w.du;
+        R = w.R;
       }
-      // compact the valid pairs to the front of the warp's record slots
+      // compact the valid pairs to the front lanes: lane i takes the i-th
+      // valid pair (register shuffles; no shared memory)
       const unsigned mask = __ballot_sync(FULL, W > 0);
       const int nv = __popc(mask);
-      if (W > 0) {
-        const int pos = __popc(mask & ((1u << lane) - 1u));
-        rec[3 * pos + 0] = r0;
-        rec[3 * pos + 1] = r1;
-        rec[3 * pos + 2] = r2;
+      if (nv == 0) continue;
+      const bool act = lane < nv;
+      // An inactive lane takes a copy of the first valid pair (its walk
+      // reads inside that pair's window and its sums are discarded).
+      const int src = mask == FULL ? lane : nth_set_bit(mask, act ? lane : 0);
+      if (mask != FULL) {
+        W = __shfl_sync(FULL, W, src);
+        klo = __shfl_sync(FULL, klo, src);
+        u0 = __shfl_sync(FULL, u0, src);
+        du = __shfl_sync(FULL, du, src);
+        R = __shfl_sync(FULL, R, src);
       }
-      __syncwarp();
-      // One pair per lane: each lane walks its own pair's whole window, eight
-      // (or four) consecutive samples per step (one 256-bit or float4
-      // residual load, predicated, issued one step ahead; packed FP32x2
-      // halves).  All pairs belong to one ball, so their windows have nearly
-      // the same length and the lanes finish together.  Samples of the
-      // aligned loads outside the window get weight 0 from the window test
-      // (u^2 <= (kappa K_S)^2, the forward's own test).
+      const int sp = s0 + src;  // sensor of this lane's pair
+      // Each lane walks its pair's whole window, eight (or four) consecutive
+      // samples per step (one 256-bit or float4 residual load, issued one
+      // step ahead; packed FP32x2 halves).  All pairs belong to one ball, so
+      // their windows have nearly the same length and the lanes finish
+      // together.  Samples of the aligned loads outside the window get
+      // weight 0 from the window test (u^2 <= (kappa K_S)^2, the forward's
+      // own test).
       const float2 one = make_float2(1.f, 1.f);
       const float4 zero4 = make_float4(0.f, 0.f, 0.f, 0.f);
-      for (int g0 = 0; g0 < nv; g0 += 32) {
-        const int i = g0 + lane;
-        const bool act = i < nv;
-        const int ii = act ? i : 0;
-        const float4 a0 = rec[3 * ii + 0], a2 = rec[3 * ii + 2];
-        const int klo = __float_as_int(a2.y);
-        const int khi = act ? klo + __float_as_int(a2.z) - 1 : -1;
-        const float *rowf = gframe + (long long)__float_as_int(a2.w) * T;
-        const float du = a0.y;
+      {
+        const int khi = act ? klo + W - 1 : -1;
+        const float *rowf = gframe + (long long)sp * T;
         float2 S1 = make_float2(0.f, 0.f), S3 = S1, SR = S1;
         // nsq = -u^2 (the exponent of E = 2^(-u^2)) from one packed multiply
         // by -u; S3 accumulates -sum g E u^3 and is negated once per pair
@@ -132,7 +139,7 @@ __device__ __forceinline__ void ball_frame_grad(const Acq &q, const float *gfram
           const int nmax = __reduce_max_sync(FULL, nit);
           int k = ka;
           float2 ua, ub, uc, ud;  // u at k, k + 1 | k + 2, k + 3 | k + 4, k + 5 | k + 6, k + 7
-          ua.x = fmaf((float)(k - klo), -du, a0.x);
+          ua.x = fmaf((float)(k - klo), -du, u0);
           ua.y = ua.x - du;
           ub.x = fmaf(-2.f, du, ua.x);
           ub.y = fmaf(-3.f, du, ua.x);
@@ -212,7 +219,7 @@ __device__ __forceinline__ void ball_frame_grad(const Acq &q, const float *gfram
           const int nmax = __reduce_max_sync(FULL, nit);
           int k = ka;
           float2 ua, ub;  // u at k, k + 1 | k + 2, k + 3
-          ua.x = fmaf((float)(k - klo), -du, a0.x);
+          ua.x = fmaf((float)(k - klo), -du, u0);
           ua.y = ua.x - du;
           ub.x = fmaf(-2.f, du, ua.x);
           ub.y = fmaf(-3.f, du, ua.x);
@@ -230,16 +237,19 @@ __device__ __forceinline__ void ball_frame_grad(const Acq &q, const float *gfram
         }
         const float s1 = S1.x + S1.y, s3 = -(S3.x + S3.y), sr = SR.x + SR.y;
         if (act) {
-          const float4 a1 = rec[3 * ii + 1];
-          gp = fmaf(s1, a0.z, gp);
-          ga = fmaf(s3, -a0.w, ga);  // record holds -A/K_S^3 for sum g E u (-u^2)
-          const float dR = fmaf(s1, a1.x, a1.y * sr);
-          gx = fmaf(dR, a1.z, gx);
-          gy = fmaf(dR, a1.w, gy);
-          gz = fmaf(dR, a2.x, gz);
+          // the pair's gradient factors (see the derivatives above)
+          const float sx = sens[sp], sy = sens[sstr + sp], sz = sens[2 * sstr + sp];
+          const float invR = __fdividef(1.f, R);
+          const float amp = 0.5f * p * invR;  // A = p/(2R)
+          const float aK = a * (1.f / K_S);   // 1/s
+          gp = fmaf(s1, 0.5f * invR * aK, gp);
+          ga = fmaf(s3, amp * (1.f / (K_S * K_S * K_S)), ga);
+          const float dR = fmaf(s1, -amp * invR * aK, amp * sr);
+          gx = fmaf(dR, (bx - sx) * invR, gx);
+          gy = fmaf(dR, (by - sy) * invR, gy);
+          gz = fmaf(dR, (bz - sz) * invR, gz);
         }
       }
-      __syncwarp();
     }
   }
   out[0] = warp_sum(gx);
@@ -257,15 +267,16 @@ __device__ __forceinline__ void load_sensors(const AdjArgs &A, float *ssens) {
   }
 }
 
-// Static mode: item = (frame, ball).
+// Static mode: item = (frame, ball).  QUEUE: persistent warps take items
+// from the work-queue counter A.queue; else a grid-stride loop (two
+// instantiations, so that each holds only its own loop's state).
+template <bool QUEUE>
 __global__ void __launch_bounds__(32 * kAdjWarps, 4) k_adjoint_static(const AdjArgs A) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
-  float4 *recs = reinterpret_cast<float4 *>(smem_raw);
-  float *ssens = reinterpret_cast<float *>(recs + kAdjWarps * 96);
+  float *ssens = reinterpret_cast<float *>(smem_raw);
   load_sensors(A, ssens);
   __syncthreads();
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-  float4 *rec = recs + warp * 96;
   bool dom = false;
   auto body = [&](long long item) {
     const int f = (int)(item / A.n);
@@ -277,7 +288,7 @@ __global__ void __launch_bounds__(32 * kAdjWarps, 4) k_adjoint_static(const AdjA
 #pragma unroll
     for (int c = 0; c < 5; ++c) v[c] = __shfl_sync(FULL, mine, c);
     float g[5];
-    ball_frame_grad<true>(A.q, A.g + (long long)f * A.q.S * A.q.T, ssens, A.q.S, rec, lane, v[0], v[1], v[2], v[3],
+    ball_frame_grad<true>(A.q, A.g + (long long)f * A.q.S * A.q.T, ssens, A.q.S, lane, v[0], v[1], v[2], v[3],
                        v[4], g, dom);
     const float sc = A.frame_scale ? __ldg(A.frame_scale + f) : 1.f;
     if (lane < 5) {
@@ -290,7 +301,7 @@ __global__ void __launch_bounds__(32 * kAdjWarps, 4) k_adjoint_static(const AdjA
       *dst = (A.flags & PA_ACCUMULATE) ? *dst + gv : gv;
     }
   };
-  if (A.queue != nullptr) {
+  if constexpr (QUEUE) {
     // Persistent warps take A.queue_chunk items at a time from the counter,
     // so a warp that drew cheap balls (small windows) takes more of them and
     // no block waits for its slowest warp.  Each item is still computed whole
@@ -319,20 +330,19 @@ __global__ void __launch_bounds__(32 * kAdjWarps, 4) k_adjoint_static(const AdjA
 // (channel, basis) slots sum the chain rule over the buffered frames and write
 // each (omega, theta, sigma) gradient once per chunk.  The deformation
 // parameters are read through L1/L2 rather than held in shared memory, which
-// keeps the block at ~30 KB of shared memory and 4 blocks per SM.
+// keeps the block at ~12 KB of shared memory (sensors and the frame buffers)
+// and 4 blocks per SM.
 constexpr int kAdj4dFrames = 32;
 
 __global__ void __launch_bounds__(32 * kAdjWarps, 4) k_adjoint_4d(const AdjArgs A) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   const int nb = A.nb;
   const int per = 5 * nb;
-  float4 *recs = reinterpret_cast<float4 *>(smem_raw);
-  float *ssens = reinterpret_cast<float *>(recs + kAdjWarps * 96);
+  float *ssens = reinterpret_cast<float *>(smem_raw);
   float *gbase = ssens + 3 * A.q.S;  // per warp: [kAdj4dFrames][5] scaled frame gradients
   load_sensors(A, ssens);
   __syncthreads();
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-  float4 *rec = recs + warp * 96;
   float *gq = gbase + warp * (kAdj4dFrames * 5);
   const float L2E_HALF = 0.72134752044448170368f;  // log2(e)/2
   const bool acc = (A.flags & PA_ACCUMULATE) != 0;
@@ -367,7 +377,7 @@ __global__ void __launch_bounds__(32 * kAdjWarps, 4) k_adjoint_4d(const AdjArgs 
           H[c] = warp_sum(h);
         }
         float g[5];
-        ball_frame_grad<false>(A.q, A.g + (long long)f * A.q.S * A.q.T, ssens, A.q.S, rec, lane, q0[0] * (1.f + H[0]),
+        ball_frame_grad<false>(A.q, A.g + (long long)f * A.q.S * A.q.T, ssens, A.q.S, lane, q0[0] * (1.f + H[0]),
                         q0[1] * (1.f + H[1]), q0[2] * (1.f + H[2]), q0[3] * (1.f + H[3]), q0[4] * (1.f + H[4]), g,
                         dom);
         const float sc = A.frame_scale ? __ldg(A.frame_scale + f) : 1.f;
@@ -427,9 +437,7 @@ __global__ void __launch_bounds__(32 * kAdjWarps, 4) k_adjoint_4d(const AdjArgs 
 // host.
 
 __global__ void __launch_bounds__(32 * kAdjWarps) k_adjoint_batched(const BatchAdjArgs A) {
-  __shared__ __align__(16) float4 recs[kAdjWarps * 96];
-  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-  float4 *rec = recs + warp * 96;
+  const int lane = threadIdx.x & 31;
   bool dom = false;
   while (true) {
     unsigned long long base = 0;
@@ -450,7 +458,7 @@ __global__ void __launch_bounds__(32 * kAdjWarps) k_adjoint_batched(const BatchA
 #pragma unroll
       for (int c = 0; c < 5; ++c) v[c] = __shfl_sync(FULL, mine, c);
       float g[5];
-      ball_frame_grad<true>(d.q, d.g + (long long)f * d.q.S * d.q.T, d.q.sensors, d.q.sstride, rec, lane, v[0], v[1], v[2],
+      ball_frame_grad<true>(d.q, d.g + (long long)f * d.q.S * d.q.T, d.q.sensors, d.q.sstride, lane, v[0], v[1], v[2],
                       v[3], v[4], g, dom);
       if (lane < 5) {
         float gv = g[0];
@@ -465,11 +473,6 @@ __global__ void __launch_bounds__(32 * kAdjWarps) k_adjoint_batched(const BatchA
   if (dom) set_error(A.err, PA_ERR_DOMAIN);
 }
 
-size_t adj_static_smem(int S) { return sizeof(float4) * kAdjWarps * 96 + sizeof(float) * 3 * (size_t)S; }
-size_t adj_4d_smem(int S, int nb) {
-  (void)nb;
-  return adj_static_smem(S) + sizeof(float) * (size_t)kAdjWarps * kAdj4dFrames * 5;
-}
 
 template <typename K>
 cudaError_t launch_gridstride(K kern, const AdjArgs &a, size_t smem, int sms, cudaStream_t st) {
@@ -487,16 +490,19 @@ cudaError_t launch_gridstride(K kern, const AdjArgs &a, size_t smem, int sms, cu
 
 }  // namespace
 
+size_t adj_static_smem(int S) { return sizeof(float) * 3 * (size_t)S; }
+size_t adj_4d_smem(int S) { return adj_static_smem(S) + sizeof(float) * (size_t)kAdjWarps * kAdj4dFrames * 5; }
+
 cudaError_t launch_adjoint_static(const AdjArgs &a0, int sms, cudaStream_t st) {
   if (a0.n_items == 0) return cudaSuccess;
   const size_t smem = adj_static_smem(a0.q.S);
-  if (a0.queue == nullptr) return launch_gridstride(k_adjoint_static, a0, smem, sms, st);
+  if (a0.queue == nullptr) return launch_gridstride(k_adjoint_static<false>, a0, smem, sms, st);
   // work queue: one wave of persistent blocks
   AdjArgs a = a0;
-  cudaError_t e = cudaFuncSetAttribute(k_adjoint_static, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  cudaError_t e = cudaFuncSetAttribute(k_adjoint_static<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   if (e != cudaSuccess) return e;
   int occ = 0;
-  e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_adjoint_static, 32 * kAdjWarps, smem);
+  e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_adjoint_static<true>, 32 * kAdjWarps, smem);
   if (e != cudaSuccess) return e;
   if (occ < 1) return cudaErrorInvalidConfiguration;
   const long long warps = (long long)sms * occ * kAdjWarps;
@@ -505,7 +511,7 @@ cudaError_t launch_adjoint_static(const AdjArgs &a0, int sms, cudaStream_t st) {
   a.queue_chunk = (int)std::max(2LL, std::min(16LL, a.n_items / (warps * 32)));
   e = cudaMemsetAsync(a.queue, 0, sizeof(unsigned long long), st);
   if (e != cudaSuccess) return e;
-  k_adjoint_static<<<(unsigned)(sms * occ), 32 * kAdjWarps, smem, st>>>(a);
+  k_adjoint_static<true><<<(unsigned)(sms * occ), 32 * kAdjWarps, smem, st>>>(a);
   return cudaGetLastError();
 }
 
@@ -538,7 +544,7 @@ cudaError_t launch_adjoint_4d(const AdjArgs &a, int sms, cudaStream_t st) {
     c.g = a.g + (long long)f0 * a.q.S * a.q.T;
     c.frame_scale = a.frame_scale ? a.frame_scale + f0 : nullptr;
     if (f0 > 0) c.flags |= PA_ACCUMULATE;
-    cudaError_t e = launch_gridstride(k_adjoint_4d, c, adj_4d_smem(a.q.S, a.nb), sms, st);
+    cudaError_t e = launch_gridstride(k_adjoint_4d, c, adj_4d_smem(a.q.S), sms, st);
     if (e != cudaSuccess) return e;
   }
   return cudaSuccess;

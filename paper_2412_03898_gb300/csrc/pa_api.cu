@@ -493,8 +493,7 @@ int32_t pa_adjoint(const pa_geom *geom, const pa_balls *balls, const pa_canon *c
     a.g_theta = grads->theta;
     a.g_sigma = grads->sigma;
     a.n_items = n;
-    const size_t smem = sizeof(float4) * 8 * 96 + sizeof(float) * 3 * (size_t)geom->n_sensors +
-                        sizeof(float) * 8 * 6 * 5 * (size_t)canon->n_basis;
+    const size_t smem = pa::adj_4d_smem(geom->n_sensors);
     if ((long long)smem > d->max_smem) return PA_ERR_INVALID_ARG;
     if (n_frames == 0) {
       // no frame contributes: gradients are zero
@@ -512,7 +511,7 @@ int32_t pa_adjoint(const pa_geom *geom, const pa_balls *balls, const pa_canon *c
   a.stride = balls->stride;
   a.n_items = (long long)n_frames * n;
   a.queue = static_cast<unsigned long long *>(workspace);
-  const size_t smem = sizeof(float4) * 8 * 96 + sizeof(float) * 3 * (size_t)geom->n_sensors;
+  const size_t smem = pa::adj_static_smem(geom->n_sensors);
   if ((long long)smem > d->max_smem) return PA_ERR_INVALID_ARG;
   return cuda_status(pa::launch_adjoint_static(a, d->sms, st));
 }
@@ -1109,7 +1108,7 @@ int32_t pa_adjoint_4d(const pa_geom *geom, const pa_canon *canon, const float *t
   if (!grads->state || !grads->omega || !grads->theta || !grads->sigma) return PA_ERR_INVALID_ARG;
   if (n_frames > 0 && (t_frames == nullptr || trace_grad == nullptr || !aligned(trace_grad, 16)))
     return PA_ERR_INVALID_ARG;
-  const size_t smem = sizeof(float4) * 8 * 96 + sizeof(float) * 3 * (size_t)geom->n_sensors;
+  const size_t smem = pa::adj_static_smem(geom->n_sensors);
   const DevInfo *d = dev_info();
   if (!d) return PA_ERR_CUDA;
   if ((long long)smem > d->max_smem) return PA_ERR_INVALID_ARG;

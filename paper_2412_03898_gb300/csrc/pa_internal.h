@@ -127,6 +127,10 @@ cudaError_t launch_forward_batched(const BatchFwdArgs &a, int group, size_t smem
 cudaError_t launch_adjoint_batched(const BatchAdjArgs &a, int sms, cudaStream_t st);
 cudaError_t launch_count(const Acq &q, const float *state, long long n, long long stride, int F,
                          unsigned long long *out, cudaStream_t st);
+// Dynamic shared memory of the static and 4D adjoint kernels (sensor
+// coordinates; 4D adds per-warp frame-gradient buffers).
+size_t adj_static_smem(int S);
+size_t adj_4d_smem(int S);
 cudaError_t launch_adjoint_static(const AdjArgs &a, int sms, cudaStream_t st);
 cudaError_t launch_adjoint_4d(const AdjArgs &a, int sms, cudaStream_t st);
 // Imaging kernels (pa_image.cu).

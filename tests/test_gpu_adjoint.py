@@ -42,6 +42,32 @@ def test_adjoint_static_parity(pa, seed, n, ns, T, F):
         assert rel_l2(got[:, ch], want[:, ch]) <= GRAD_TOL, name
 
 
+@pytest.mark.parametrize("T", [516, 520])
+def test_adjoint_static_sensor_chunks_with_invalid_and_clipped_pairs(pa, T):
+    """Sensors at three radii mixed within every 32-sensor chunk: windows
+    inside the trace, windows clipped by its last sample, and windows past
+    its end (no samples at all), so that the kernel compacts the valid pairs
+    of a chunk and walks clipped windows.  T = 516 takes the float4 walk,
+    T = 520 the 256-bit one."""
+    sc = pa_inputs.small_scene(seed=17, n_balls=300, n_sensors=70, n_samples=T)
+    n = sc.n_balls
+    rng = np.random.default_rng(17)
+    end = sc.c * (sc.t0 + (T - 1) / sc.fs)  # distance of the last sample
+    scale = np.array([1.0, end / 40.0, 2.0], np.float32)[rng.integers(0, 3, sc.n_sensors)]
+    sens = (sc.sensors * scale[None, :]).astype(np.float32)
+    g = rng.standard_normal((1, sc.n_sensors, T)).astype(np.float32)
+    geom = geometry(sc, sensors=sens)
+    st = dev_pad(sc.balls)[None].contiguous()
+    got = pa.adjoint(geom, torch.from_numpy(g).cuda(), state=st, n=n)
+    pa.device_error()
+    fixed = pa.adjoint(geom, torch.from_numpy(g).cuda(), state=st, n=n, queue=False)
+    assert torch.equal(got[..., :n], fixed[..., :n])
+    want = oracle.adjoint_state(sc.balls[None], sens, *_geom_args(sc), g)
+    got = got[..., :n].cpu().numpy()
+    for ch, name in enumerate("xyzap"):
+        assert rel_l2(got[:, ch], want[:, ch]) <= GRAD_TOL, name
+
+
 def test_adjoint_frame_scale_and_accumulate(pa):
     sc = pa_inputs.small_scene(seed=13, n_balls=100, n_sensors=8, n_samples=512, n_frames=2)
     rng = np.random.default_rng(1)
