@@ -38,6 +38,11 @@ namespace pa {
 namespace {
 
 constexpr int kAdjWarps = 8;
+// Static mode runs one block of 32 warps per SM: its shared memory is one
+// copy of the sensor table per SM, which leaves the most L1 to the residual
+// rows that neighbouring balls re-read (8-warp blocks, four per SM, hold four
+// copies and measured 4% slower with 37% more L2 traffic).
+constexpr int kAdjStaticWarps = 32;
 
 // dL/d(x, y, z, a, p) of one ball at frame f, summed over all sensors and
 // samples.  Returns the totals (identical in every lane).
@@ -271,7 +276,7 @@ __device__ __forceinline__ void load_sensors(const AdjArgs &A, float *ssens) {
 // from the work-queue counter A.queue; else a grid-stride loop (two
 // instantiations, so that each holds only its own loop's state).
 template <bool QUEUE>
-__global__ void __launch_bounds__(32 * kAdjWarps, 4) k_adjoint_static(const AdjArgs A) {
+__global__ void __launch_bounds__(32 * kAdjStaticWarps, 1) k_adjoint_static(const AdjArgs A) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   float *ssens = reinterpret_cast<float *>(smem_raw);
   load_sensors(A, ssens);
@@ -315,8 +320,8 @@ __global__ void __launch_bounds__(32 * kAdjWarps, 4) k_adjoint_static(const AdjA
       for (long long item = (long long)base; item < end; ++item) body(item);
     }
   } else {
-    for (long long item = (long long)blockIdx.x * kAdjWarps + warp; item < A.n_items;
-         item += (long long)gridDim.x * kAdjWarps)
+    for (long long item = (long long)blockIdx.x * kAdjStaticWarps + warp; item < A.n_items;
+         item += (long long)gridDim.x * kAdjStaticWarps)
       body(item);
   }
   if (dom) set_error(A.err, PA_ERR_DOMAIN);
@@ -474,17 +479,19 @@ __global__ void __launch_bounds__(32 * kAdjWarps) k_adjoint_batched(const BatchA
 }
 
 
+// Grid-stride launch of a kernel with `warps` warps per block and one item
+// per warp and trip.
 template <typename K>
-cudaError_t launch_gridstride(K kern, const AdjArgs &a, size_t smem, int sms, cudaStream_t st) {
+cudaError_t launch_gridstride(K kern, int warps, const AdjArgs &a, size_t smem, int sms, cudaStream_t st) {
   cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   if (e != cudaSuccess) return e;
   int occ = 0;
-  e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, kern, 32 * kAdjWarps, smem);
+  e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, kern, 32 * warps, smem);
   if (e != cudaSuccess) return e;
   if (occ < 1) return cudaErrorInvalidConfiguration;
-  const long long need = (a.n_items + kAdjWarps - 1) / kAdjWarps;
+  const long long need = (a.n_items + warps - 1) / warps;
   const long long grid = std::max(1LL, std::min(need, (long long)sms * occ * 4));
-  kern<<<(unsigned)grid, 32 * kAdjWarps, smem, st>>>(a);
+  kern<<<(unsigned)grid, 32 * warps, smem, st>>>(a);
   return cudaGetLastError();
 }
 
@@ -496,22 +503,22 @@ size_t adj_4d_smem(int S) { return adj_static_smem(S) + sizeof(float) * (size_t)
 cudaError_t launch_adjoint_static(const AdjArgs &a0, int sms, cudaStream_t st) {
   if (a0.n_items == 0) return cudaSuccess;
   const size_t smem = adj_static_smem(a0.q.S);
-  if (a0.queue == nullptr) return launch_gridstride(k_adjoint_static<false>, a0, smem, sms, st);
+  if (a0.queue == nullptr) return launch_gridstride(k_adjoint_static<false>, kAdjStaticWarps, a0, smem, sms, st);
   // work queue: one wave of persistent blocks
   AdjArgs a = a0;
   cudaError_t e = cudaFuncSetAttribute(k_adjoint_static<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   if (e != cudaSuccess) return e;
   int occ = 0;
-  e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_adjoint_static<true>, 32 * kAdjWarps, smem);
+  e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_adjoint_static<true>, 32 * kAdjStaticWarps, smem);
   if (e != cudaSuccess) return e;
   if (occ < 1) return cudaErrorInvalidConfiguration;
-  const long long warps = (long long)sms * occ * kAdjWarps;
+  const long long warps = (long long)sms * occ * kAdjStaticWarps;
   // items per grab: small enough that the tail is short (about 1/32 of a
   // warp's share), at least 2 and at most 16 to bound the atomics
   a.queue_chunk = (int)std::max(2LL, std::min(16LL, a.n_items / (warps * 32)));
   e = cudaMemsetAsync(a.queue, 0, sizeof(unsigned long long), st);
   if (e != cudaSuccess) return e;
-  k_adjoint_static<true><<<(unsigned)(sms * occ), 32 * kAdjWarps, smem, st>>>(a);
+  k_adjoint_static<true><<<(unsigned)(sms * occ), 32 * kAdjStaticWarps, smem, st>>>(a);
   return cudaGetLastError();
 }
 
@@ -544,7 +551,7 @@ cudaError_t launch_adjoint_4d(const AdjArgs &a, int sms, cudaStream_t st) {
     c.g = a.g + (long long)f0 * a.q.S * a.q.T;
     c.frame_scale = a.frame_scale ? a.frame_scale + f0 : nullptr;
     if (f0 > 0) c.flags |= PA_ACCUMULATE;
-    cudaError_t e = launch_gridstride(k_adjoint_4d, c, adj_4d_smem(a.q.S), sms, st);
+    cudaError_t e = launch_gridstride(k_adjoint_4d, kAdjWarps, c, adj_4d_smem(a.q.S), sms, st);
     if (e != cudaSuccess) return e;
   }
   return cudaSuccess;
