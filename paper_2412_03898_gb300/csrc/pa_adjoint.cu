@@ -9,7 +9,7 @@
 //    (ball, sensor) pairs in parallel and compact the valid ones to the
 //    front lanes with register shuffles; then each lane walks one pair's window,
 //    eight consecutive samples per step (one 256-bit residual load from L2
-//    when the rows are 32-byte aligned, else four samples per float4 load;
+//    when the rows are 32-byte aligned, else two float4 loads;
 //    packed FP32x2 arithmetic; the next step's load in flight, unpredicated
 //    and double-buffered on the steps inside every lane's window),
 //    accumulating
@@ -58,14 +58,19 @@ __device__ __forceinline__ int nth_set_bit(unsigned m, int i) {
   return lo;
 }
 
-template <bool ALLOW_WIDE>
+// Walk forms: eight samples per step from one 256-bit load (rows 32-byte
+// aligned) or from two float4 loads; kWalkAuto picks per call.
+enum WalkForm { kWalkFloat4 = 0, kWalkWide = 1, kWalkAuto = 2 };
+
+template <int WALK>
 __device__ __forceinline__ void ball_frame_grad(const Acq &q, const float *gframe, const float *sens, int sstr,
                                                 int lane, float bx, float by, float bz, float a, float p,
                                                 float out[5], bool &dom) {
   const int S = q.S, T = q.T;
   const float umax2 = (q.kappa * K_S) * (q.kappa * K_S);  // the forward's window test u^2 <= umax2
   // 256-bit residual loads need 32-byte aligned rows
-  const bool wide = ALLOW_WIDE && (T & 7) == 0 && (reinterpret_cast<uintptr_t>(gframe) & 31) == 0;
+  const bool wide = WALK == kWalkWide ||
+                    (WALK == kWalkAuto && (T & 7) == 0 && (reinterpret_cast<uintptr_t>(gframe) & 31) == 0);
   float gx = 0.f, gy = 0.f, gz = 0.f, ga = 0.f, gp = 0.f;
   if (a > 0.f && p != 0.f) {
     for (int s0 = 0; s0 < S; s0 += 32) {
@@ -135,11 +140,16 @@ __device__ __forceinline__ void ball_frame_grad(const Acq &q, const float *gfram
           S3 = __ffma2_rn(gu, nsq, S3);
           SR = __ffma2_rn(ge, __ffma2_rn(nsq, pk2, one), SR);
         };
-        if (wide) {
-          // 256-bit loads from a 32-byte aligned start (rows are 32-byte
-          // aligned when T % 8 == 0; a load starting at k <= khi <= T - 1
-          // with k % 8 == 0 ends at k + 7 <= T - 1)
-          const int ka = klo & ~7;
+        // The walk, eight samples per step.  WIDE: one 256-bit load per step
+        // from a 32-byte aligned start (rows are 32-byte aligned when
+        // T % 8 == 0; a load starting at k <= khi <= T - 1 with k % 8 == 0
+        // ends at k + 7 <= T - 1).  Else two float4 loads from a 16-byte
+        // aligned start (T % 4 == 0), the second one predicated on starting
+        // inside the walk (a float4 starting at k <= khi with k % 4 == 0 ends
+        // at k + 3 <= T - 1).
+        auto walk = [&](auto W) {
+          constexpr bool WIDE = decltype(W)::value;
+          const int ka = WIDE ? (klo & ~7) : (klo & ~3);
           const int nit = act ? ((khi - ka) >> 3) + 1 : 0;
           const int nmax = __reduce_max_sync(FULL, nit);
           int k = ka;
@@ -154,6 +164,20 @@ __device__ __forceinline__ void ball_frame_grad(const Acq &q, const float *gfram
           ud.y = fmaf(-7.f, du, ua.x);
           const float2 nd8 = make_float2(-8.f * du, -8.f * du);
           const float *pk = rowf + k;
+          // the step starting at p = pk + off, k + off: predicated on lying in
+          // the walk (x keeps its zeros past it) or, for the first half of a
+          // step inside every lane's walk, unpredicated
+          auto load = [&](int off, bool first_in_walk, float4 &x0, float4 &x1) {
+            if constexpr (WIDE) {
+              if (first_in_walk)
+                ldg8(pk + off, x0, x1);
+              else
+                ldg8_if(pk + off, k + off <= khi, x0, x1);
+            } else {
+              if (first_in_walk || k + off <= khi) x0 = __ldg(reinterpret_cast<const float4 *>(pk + off));
+              if (k + off + 4 <= khi) x1 = __ldg(reinterpret_cast<const float4 *>(pk + off + 4));
+            }
+          };
           auto eval = [&](auto masked, const float4 &x0, const float4 &x1) {
             if (decltype(masked)::value) {
               half(ua, make_float2(x0.x, x0.y));
@@ -177,7 +201,7 @@ __device__ __forceinline__ void ball_frame_grad(const Acq &q, const float *gfram
           // lying in the walk (zeros past it).
           auto edge_step = [&](float4 &c0, float4 &c1) {
             float4 n0 = zero4, n1 = zero4;
-            ldg8_if(pk + 8, k + 8 <= khi, n0, n1);
+            load(8, false, n0, n1);
             eval(std::true_type{}, c0, c1);
             c0 = n0;
             c1 = n1;
@@ -193,52 +217,39 @@ __device__ __forceinline__ void ball_frame_grad(const Acq &q, const float *gfram
           const int mn = __reduce_min_sync(FULL, act ? nit : 0x7fffffff);
           const int e1 = min(mn - 1, nmax);
           float4 c0 = zero4, c1 = zero4;
-          ldg8_if(pk, k <= khi, c0, c1);
+          load(0, false, c0, c1);
           int it = 0;
           if (nmax > 0) {
             edge_step(c0, c1);
             ++it;
           }
           for (; it + 1 < e1; it += 2) {  // two interior steps, loads double-buffered
-            float4 n0, n1;
-            ldg8(pk + 8, n0, n1);
+            float4 n0 = zero4, n1 = zero4;
+            load(8, true, n0, n1);
             eval(std::false_type{}, c0, c1);
-            ldg8(pk + 8, c0, c1);
+            if constexpr (!WIDE) c1 = zero4;
+            load(8, true, c0, c1);
             eval(std::false_type{}, n0, n1);
           }
           if (it < e1) {
-            float4 n0, n1;
-            ldg8(pk + 8, n0, n1);
+            float4 n0 = zero4, n1 = zero4;
+            load(8, true, n0, n1);
             eval(std::false_type{}, c0, c1);
             c0 = n0;
             c1 = n1;
             ++it;
           }
           for (; it < nmax; ++it) edge_step(c0, c1);
+        };
+        if constexpr (WALK == kWalkWide) {
+          walk(std::true_type{});
+        } else if constexpr (WALK == kWalkFloat4) {
+          walk(std::false_type{});
         } else {
-          // float4 loads: rows start 16-byte aligned (T % 4 == 0), and a
-          // float4 starting at k <= khi <= T - 1 with k % 4 == 0 ends at
-          // k + 3 <= T - 1
-          const int ka = klo & ~3;
-          const int nit = act ? ((khi - ka) >> 2) + 1 : 0;
-          const int nmax = __reduce_max_sync(FULL, nit);
-          int k = ka;
-          float2 ua, ub;  // u at k, k + 1 | k + 2, k + 3
-          ua.x = fmaf((float)(k - klo), -du, u0);
-          ua.y = ua.x - du;
-          ub.x = fmaf(-2.f, du, ua.x);
-          ub.y = fmaf(-3.f, du, ua.x);
-          const float2 nd4 = make_float2(-4.f * du, -4.f * du);
-          const float4 *row = reinterpret_cast<const float4 *>(rowf);
-          float4 gcur = k <= khi ? __ldg(row + (k >> 2)) : zero4;
-          for (int it = 0; it < nmax; ++it, k += 4) {
-            const float4 gnext = k + 4 <= khi ? __ldg(row + ((k + 4) >> 2)) : zero4;
-            half(ua, make_float2(gcur.x, gcur.y));
-            half(ub, make_float2(gcur.z, gcur.w));
-            ua = __fadd2_rn(ua, nd4);
-            ub = __fadd2_rn(ub, nd4);
-            gcur = gnext;
-          }
+          if (wide)
+            walk(std::true_type{});
+          else
+            walk(std::false_type{});
         }
         const float s1 = S1.x + S1.y, s3 = -(S3.x + S3.y), sr = SR.x + SR.y;
         if (act) {
@@ -273,9 +284,11 @@ __device__ __forceinline__ void load_sensors(const AdjArgs &A, float *ssens) {
 }
 
 // Static mode: item = (frame, ball).  QUEUE: persistent warps take items
-// from the work-queue counter A.queue; else a grid-stride loop (two
-// instantiations, so that each holds only its own loop's state).
-template <bool QUEUE>
+// from the work-queue counter A.queue; else a grid-stride loop.  WIDE: the
+// residual rows are 32-byte aligned (256-bit loads), else float4 loads.
+// (One instantiation per combination, so that each holds only its own
+// loop's and walk's state.)
+template <bool QUEUE, bool WIDE>
 __global__ void __launch_bounds__(32 * kAdjStaticWarps, 1) k_adjoint_static(const AdjArgs A) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   float *ssens = reinterpret_cast<float *>(smem_raw);
@@ -293,7 +306,8 @@ __global__ void __launch_bounds__(32 * kAdjStaticWarps, 1) k_adjoint_static(cons
 #pragma unroll
     for (int c = 0; c < 5; ++c) v[c] = __shfl_sync(FULL, mine, c);
     float g[5];
-    ball_frame_grad<true>(A.q, A.g + (long long)f * A.q.S * A.q.T, ssens, A.q.S, lane, v[0], v[1], v[2], v[3],
+    ball_frame_grad<WIDE ? kWalkWide : kWalkFloat4>(A.q, A.g + (long long)f * A.q.S * A.q.T, ssens, A.q.S, lane,
+                                                     v[0], v[1], v[2], v[3],
                        v[4], g, dom);
     const float sc = A.frame_scale ? __ldg(A.frame_scale + f) : 1.f;
     if (lane < 5) {
@@ -382,7 +396,7 @@ __global__ void __launch_bounds__(32 * kAdjWarps, 4) k_adjoint_4d(const AdjArgs 
           H[c] = warp_sum(h);
         }
         float g[5];
-        ball_frame_grad<false>(A.q, A.g + (long long)f * A.q.S * A.q.T, ssens, A.q.S, lane, q0[0] * (1.f + H[0]),
+        ball_frame_grad<kWalkFloat4>(A.q, A.g + (long long)f * A.q.S * A.q.T, ssens, A.q.S, lane, q0[0] * (1.f + H[0]),
                         q0[1] * (1.f + H[1]), q0[2] * (1.f + H[2]), q0[3] * (1.f + H[3]), q0[4] * (1.f + H[4]), g,
                         dom);
         const float sc = A.frame_scale ? __ldg(A.frame_scale + f) : 1.f;
@@ -463,7 +477,7 @@ __global__ void __launch_bounds__(32 * kAdjWarps) k_adjoint_batched(const BatchA
 #pragma unroll
       for (int c = 0; c < 5; ++c) v[c] = __shfl_sync(FULL, mine, c);
       float g[5];
-      ball_frame_grad<true>(d.q, d.g + (long long)f * d.q.S * d.q.T, d.q.sensors, d.q.sstride, lane, v[0], v[1], v[2],
+      ball_frame_grad<kWalkAuto>(d.q, d.g + (long long)f * d.q.S * d.q.T, d.q.sensors, d.q.sstride, lane, v[0], v[1], v[2],
                       v[3], v[4], g, dom);
       if (lane < 5) {
         float gv = g[0];
@@ -500,16 +514,18 @@ cudaError_t launch_gridstride(K kern, int warps, const AdjArgs &a, size_t smem, 
 size_t adj_static_smem(int S) { return sizeof(float) * 3 * (size_t)S; }
 size_t adj_4d_smem(int S) { return adj_static_smem(S) + sizeof(float) * (size_t)kAdjWarps * kAdj4dFrames * 5; }
 
-cudaError_t launch_adjoint_static(const AdjArgs &a0, int sms, cudaStream_t st) {
-  if (a0.n_items == 0) return cudaSuccess;
+template <bool WIDE>
+cudaError_t launch_adjoint_static_form(const AdjArgs &a0, int sms, cudaStream_t st) {
   const size_t smem = adj_static_smem(a0.q.S);
-  if (a0.queue == nullptr) return launch_gridstride(k_adjoint_static<false>, kAdjStaticWarps, a0, smem, sms, st);
+  if (a0.queue == nullptr)
+    return launch_gridstride(k_adjoint_static<false, WIDE>, kAdjStaticWarps, a0, smem, sms, st);
   // work queue: one wave of persistent blocks
   AdjArgs a = a0;
-  cudaError_t e = cudaFuncSetAttribute(k_adjoint_static<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  cudaError_t e =
+      cudaFuncSetAttribute(k_adjoint_static<true, WIDE>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   if (e != cudaSuccess) return e;
   int occ = 0;
-  e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_adjoint_static<true>, 32 * kAdjStaticWarps, smem);
+  e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_adjoint_static<true, WIDE>, 32 * kAdjStaticWarps, smem);
   if (e != cudaSuccess) return e;
   if (occ < 1) return cudaErrorInvalidConfiguration;
   const long long warps = (long long)sms * occ * kAdjStaticWarps;
@@ -518,8 +534,15 @@ cudaError_t launch_adjoint_static(const AdjArgs &a0, int sms, cudaStream_t st) {
   a.queue_chunk = (int)std::max(2LL, std::min(16LL, a.n_items / (warps * 32)));
   e = cudaMemsetAsync(a.queue, 0, sizeof(unsigned long long), st);
   if (e != cudaSuccess) return e;
-  k_adjoint_static<true><<<(unsigned)(sms * occ), 32 * kAdjStaticWarps, smem, st>>>(a);
+  k_adjoint_static<true, WIDE><<<(unsigned)(sms * occ), 32 * kAdjStaticWarps, smem, st>>>(a);
   return cudaGetLastError();
+}
+
+cudaError_t launch_adjoint_static(const AdjArgs &a, int sms, cudaStream_t st) {
+  if (a.n_items == 0) return cudaSuccess;
+  // every frame's rows are 32-byte aligned when the base is and T % 8 == 0
+  const bool wide = (a.q.T & 7) == 0 && (reinterpret_cast<uintptr_t>(a.g) & 31) == 0;
+  return wide ? launch_adjoint_static_form<true>(a, sms, st) : launch_adjoint_static_form<false>(a, sms, st);
 }
 
 cudaError_t launch_adjoint_batched(const BatchAdjArgs &a, int sms, cudaStream_t st) {
