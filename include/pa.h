@@ -282,7 +282,7 @@ PA_API int32_t pa_forward_batched(const pa_scene *scenes, int32_t n_scenes, uint
 /* Static-mode adjoint of several scenes in one persistent launch: warps take
  * chunks of (scene, frame, ball) items from a counter in the workspace,
  * scenes with the most sensors first; plan: its items per grab, or NULL
- * (8).  Each scene's grad_state equals pa_adjoint's static mode.  flags:
+ * (1).  Each scene's grad_state equals pa_adjoint's static mode.  flags:
  * PA_ACCUMULATE. */
 PA_API int32_t pa_adjoint_batched(const pa_scene *scenes, int32_t n_scenes, uint32_t flags, const pa_plan *plan,
                                   void *workspace, size_t workspace_bytes, void *stream);

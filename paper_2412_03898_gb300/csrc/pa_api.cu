@@ -277,7 +277,7 @@ constexpr int32_t kTileCandidates[][5] = {
     {16, 1536, 256, 0, 16}, {16, 1024, 512, 0, 16}, {8, 2048, 512, 0, 16}, {16, 1536, 512, 0, 4},
 };
 constexpr int kNumTileCandidates = sizeof(kTileCandidates) / sizeof(kTileCandidates[0]);
-constexpr int32_t kAdjChunkCandidates[] = {4, 8, 16, 32};
+constexpr int32_t kAdjChunkCandidates[] = {1, 2, 4, 8, 16};
 
 // Bytes at the start of a batched or pa_adjoint_4d workspace: its work-queue
 // counter.
@@ -642,7 +642,7 @@ int32_t pa_adjoint_batched(const pa_scene *scenes, int32_t n_scenes, uint32_t fl
   pa::BatchAdjArgs a;
   std::memset(&a, 0, sizeof(a));
   a.n_scenes = m;
-  a.chunk = plan && plan->adj_chunk > 0 ? plan->adj_chunk : 8;
+  a.chunk = plan && plan->adj_chunk > 0 ? plan->adj_chunk : 1;
   a.counter = static_cast<unsigned long long *>(workspace);
   a.flags = flags;
   a.err = d->err;
