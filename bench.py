@@ -108,6 +108,8 @@ def parse():
     ap.add_argument("--no-batched", action="store_true", help="skip the 16-scene batched comparison")
     ap.add_argument("--steps-batched", type=int, default=2)
     ap.add_argument("--no-autotune", action="store_true")
+    ap.add_argument("--no-spatial-order", action="store_true",
+                    help="keep the generator's ball order instead of storing the cloud in Morton order")
     ap.add_argument("--no-imaging", action="store_true", help="skip the UBP / splat / MAP / SSIM leg")
     ap.add_argument("--no-static", action="store_true",
                     help="skip the static-100k headline step (prints the other legs only; for profiling a leg)")
@@ -334,6 +336,11 @@ def run_ours(args):
     n = sc.n_balls
     to_dev = lambda a: pa.pad_last(torch.from_numpy(np.ascontiguousarray(a, dtype=np.float32)).to(dev))
     state = to_dev(sc.balls)[None].contiguous()
+    if not args.no_spatial_order:
+        # storage layout (set-up, not timed): the cloud in Morton order of its
+        # centres, by the library's own pa_spatial_order; every sum of the step
+        # is over all balls, so only the forward's tile boxes change
+        state = pa.gather_rows(state, pa.spatial_order(state, n))
     sensors = torch.from_numpy(sc.sensors).to(dev)
     geom = pa.Geometry(sensors, sc.c, sc.fs, sc.t0, sc.n_samples, sc.kappa)
     # measured data: the forward of a perturbed cloud (GT differs from the model)
@@ -446,6 +453,8 @@ def run_ours(args):
                    "n_samples": geom.n_samples, "contributions_per_step": C,
                    "l2": "flushed (512 MB write) before every timed step", "forward_plan": plan,
                    "forward_tiles": "autotuned" if tiles is not None else "default",
+                   "ball_order": "generator (tubes)" if args.no_spatial_order
+                   else "Morton order of the centres (pa_spatial_order, set-up)",
                    "parallelism": f"replicas x{world}"},
         "clocks": clocks,
         "e2e": {"value": world * C * args.steps / (e2e_ms * 1e-3), "unit": UNIT, "h2d_bytes_per_step": e2e_in,
@@ -491,9 +500,14 @@ def bench_4d(args, pa, pa_inputs, dev, flush):
     canon = to_dev(sc.balls).contiguous()
     nb = 65
     deform = init_deformation(nb, canon.shape[-1], dev, omega_scale=0.02, seed=1)
+    if not args.no_spatial_order:
+        # storage layout (set-up): Morton order of the canonical centres
+        perm = pa.spatial_order(canon, n)
+        canon, deform = pa.gather_rows(canon, perm), pa.gather_rows(deform, perm)
     del gt
     out = {"workload": f"{sc.name}: {n} canonical balls, {F} frames, Nb={nb}, {sc.n_sensors} sensors, "
-                       f"{sc.n_samples} samples", "steps": args.steps_4d}
+                       f"{sc.n_samples} samples", "steps": args.steps_4d,
+           "ball_order": "generator (tubes)" if args.no_spatial_order else "Morton (pa_spatial_order, set-up)"}
     C = pa.count_contributions(geom, pa.deform_balls(canon, deform[0], deform[1], deform[2], t, n), n)
     out["contributions_per_iter"] = C
     res = {}
@@ -665,9 +679,14 @@ def bench_large4d(args, pa, pa_inputs, dev):
     base = torch.cuda.memory_allocated(dev)
     t = torch.from_numpy(pa_inputs.frame_times(F)).to(dev)
     canon = to_dev(sc.balls).contiguous()
+    if not args.no_spatial_order:
+        # storage layout (set-up): Morton order of the canonical centres (the
+        # initial deformation is the same for every ball)
+        canon = pa.gather_rows(canon, pa.spatial_order(canon, n))
     ir = GGBallIR(geom, canon, init_deformation(65, canon.shape[-1], dev), t, meas, n)
     out = {"workload": f"{sc.name}: {n} balls, {F} frames, Nb = 65, {geom.n_sensors} sensors, {geom.n_samples} "
-                       "samples", "contributions_per_iteration": C}
+                       "samples", "contributions_per_iteration": C,
+           "ball_order": "generator (tubes)" if args.no_spatial_order else "Morton (pa_spatial_order, set-up)"}
 
     def timed(fn, iters):
         torch.cuda.synchronize()

@@ -304,6 +304,41 @@ def adjoint(geom: Geometry, trace_grad: torch.Tensor, state: Optional[torch.Tens
     return out
 
 
+def spatial_order(state: torch.Tensor, n: Optional[int] = None,
+                  workspace: Optional[torch.Tensor] = None) -> torch.Tensor:
+    """Morton (Z-curve) order of the ball centres of frame 0 of `state`
+    ([F, 5, stride] or [5, stride]): an int32 permutation perm [n] such that
+    position i of the reordered cloud holds ball perm[i] (pa_spatial_order).
+    Apply it with gather_rows; a cloud stored in this order makes the
+    forward's ball tiles compact in space."""
+    state, bs, n = _balls_struct(state, n)
+    perm = torch.empty(max(n, 1), dtype=torch.int32, device=state.device)[:n]
+    need = int(_LIB.pa_spatial_order_workspace_size(n))
+    workspace = _workspace(workspace, max(need, 256), state.device)
+    _lib.check(_LIB.pa_spatial_order(ctypes.byref(bs), perm.data_ptr() if n > 0 else None, workspace.data_ptr(),
+                                     workspace.numel(), _stream()), "pa_spatial_order")
+    return perm
+
+
+def gather_rows(x: torch.Tensor, perm: torch.Tensor, out: Optional[torch.Tensor] = None) -> torch.Tensor:
+    """out[..., i] = x[..., perm[i]] for i < len(perm) over every leading row
+    of a contiguous [..., stride] tensor (pa_gather_rows); the padding
+    columns of a new `out` are zero."""
+    _check(x, "x")
+    _check(perm, "perm", torch.int32)
+    stride = int(x.shape[-1])
+    n = int(perm.numel())
+    rows = x.numel() // stride if stride > 0 else 0
+    if out is None:
+        out = torch.zeros_like(x)
+    _check(out, "out")
+    if out.shape != x.shape:
+        raise ValueError("out must have the shape of x")
+    _lib.check(_LIB.pa_gather_rows(x.data_ptr(), out.data_ptr(), n, stride, rows, perm.data_ptr(), _stream()),
+               "pa_gather_rows")
+    return out
+
+
 def residual_loss(pred: torch.Tensor, meas: torch.Tensor, frame_scale: Optional[torch.Tensor] = None,
                   want_loss: bool = True, want_resid: bool = False, loss_out: Optional[torch.Tensor] = None,
                   resid_out: Optional[torch.Tensor] = None, workspace: Optional[torch.Tensor] = None):

@@ -106,6 +106,9 @@ def load() -> ctypes.CDLL:
         "pa_forward_4d": (i32, [G, C, P, i32, P, u32, P, P, sz, P]),
         "pa_adjoint_4d_workspace_size": (sz, [G, C, i32, P]),
         "pa_adjoint_4d": (i32, [G, C, P, i32, P, P, GR, u32, P, P, sz, P]),
+        "pa_spatial_order_workspace_size": (sz, [i64]),
+        "pa_spatial_order": (i32, [B, P, P, sz, P]),
+        "pa_gather_rows": (i32, [P, P, i64, i64, i32, P, P]),
         "pa_loss_workspace_size": (sz, [i64, i32]),
         "pa_residual_loss": (i32, [P, P, i64, i32, P, P, P, P, sz, P]),
         "pa_residual_loss_noalloc": (i32, [P, P, i64, i32, P, P, P, P]),
@@ -152,6 +155,7 @@ def exported_symbols() -> list[str]:
             "pa_batched_workspace_size", "pa_forward_batched", "pa_adjoint_batched", "pa_plan_workspace_size",
             "pa_plan_create", "pa_plan_from_values", "pa_plan_get", "pa_plan_destroy",
             "pa_forward_4d_workspace_size", "pa_forward_4d", "pa_adjoint_4d_workspace_size", "pa_adjoint_4d",
+            "pa_spatial_order_workspace_size", "pa_spatial_order", "pa_gather_rows",
             "pa_loss_workspace_size", "pa_residual_loss", "pa_residual_loss_noalloc", "pa_sumsq", "pa_count_contributions", "pa_adam_step",
             "pa_adam_step_scheduled", "pa_step_increment", "pa_ubp_filter", "pa_ubp", "pa_splat", "pa_map",
             "pa_ssim_workspace_size", "pa_ssim", "pa_selftest_bounded_wait", "pa_measure_unit_rates"]

@@ -14,7 +14,8 @@ ROOT = os.path.dirname(HERE)
 CSRC = os.path.join(HERE, "csrc")
 LIB = os.path.join(HERE, "libpa.so")
 BUILD_DIR = os.path.join(HERE, "_build")
-UNITS = ["pa_api.cu", "pa_forward.cu", "pa_adjoint.cu", "pa_misc.cu", "pa_noalloc.cu", "pa_image.cu", "pa_probe.cu"]
+UNITS = ["pa_api.cu", "pa_forward.cu", "pa_adjoint.cu", "pa_misc.cu", "pa_noalloc.cu", "pa_image.cu", "pa_probe.cu",
+         "pa_order.cu"]
 HEADERS = [os.path.join(CSRC, "pa_common.cuh"), os.path.join(CSRC, "pa_internal.h"),
            os.path.join(ROOT, "include", "pa.h")]
 NVCC_FLAGS = ["-std=c++17", "-O3", "-lineinfo", "-gencode", "arch=compute_103a,code=sm_103a",

@@ -665,6 +665,36 @@ int32_t pa_adjoint_batched(const pa_scene *scenes, int32_t n_scenes, uint32_t fl
   return cuda_status(pa::launch_adjoint_batched(a, d->sms, static_cast<cudaStream_t>(stream)));
 }
 
+size_t pa_spatial_order_workspace_size(int64_t n) {
+  if (n <= 0 || n > INT32_MAX) return 0;
+  return pa::spatial_order_workspace(n);
+}
+
+int32_t pa_spatial_order(const pa_balls *balls, int32_t *perm, void *workspace, size_t workspace_bytes,
+                         void *stream) {
+  int rc = check_balls(balls);
+  if (rc) return rc;
+  if (balls->n > INT32_MAX) return PA_ERR_INVALID_ARG;
+  if (balls->n == 0) return PA_OK;
+  if (perm == nullptr || !aligned(perm, 4)) return PA_ERR_INVALID_ARG;
+  if (workspace == nullptr || workspace_bytes < pa::spatial_order_workspace(balls->n) || !aligned(workspace, 256))
+    return PA_ERR_WORKSPACE;
+  const DevInfo *d = dev_info();
+  if (!d) return PA_ERR_CUDA;
+  return cuda_status(pa::launch_spatial_order(balls->state, balls->stride, balls->n, perm, workspace, d->sms,
+                                              static_cast<cudaStream_t>(stream)));
+}
+
+int32_t pa_gather_rows(const float *in, float *out, int64_t n, int64_t stride, int32_t rows, const int32_t *perm,
+                       void *stream) {
+  if (n < 0 || stride < n || rows < 0 || n > INT32_MAX) return PA_ERR_INVALID_ARG;
+  if (n == 0 || rows == 0) return PA_OK;
+  if (in == nullptr || out == nullptr || perm == nullptr || in == out) return PA_ERR_INVALID_ARG;
+  const DevInfo *d = dev_info();
+  if (!d) return PA_ERR_CUDA;
+  return cuda_status(pa::launch_gather_rows(in, out, n, stride, rows, perm, d->sms, static_cast<cudaStream_t>(stream)));
+}
+
 size_t pa_loss_workspace_size(int64_t per_frame, int32_t n_frames) {
   if (per_frame <= 0 || n_frames <= 0) return 0;
   return sizeof(double) * (size_t)n_frames * pa::loss_blocks_per_frame(per_frame);

@@ -132,6 +132,12 @@ cudaError_t launch_count(const Acq &q, const float *state, long long n, long lon
 size_t adj_static_smem(int S);
 size_t adj_4d_smem(int S);
 cudaError_t launch_adjoint_static(const AdjArgs &a, int sms, cudaStream_t st);
+// Spatial (Morton) order of a cloud and the row gather that applies it.
+size_t spatial_order_workspace(long long n);
+cudaError_t launch_spatial_order(const float *state, long long stride, long long n, int *perm, void *ws, int sms,
+                                 cudaStream_t st);
+cudaError_t launch_gather_rows(const float *in, float *out, long long n, long long stride, int rows,
+                               const int *perm, int sms, cudaStream_t st);
 cudaError_t launch_adjoint_4d(const AdjArgs &a, int sms, cudaStream_t st);
 // Imaging kernels (pa_image.cu).
 struct UbpArgs {

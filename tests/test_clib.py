@@ -185,6 +185,24 @@ def test_4d_calls_and_probe_reject_bad_args_on_host(lib):
     assert lib.pa_measure_unit_rates(None, None) == E
 
 
+def test_spatial_order_and_gather_args_checked_on_host(lib):
+    from paper_2412_03898_gb300 import _lib
+    E, W = _lib.PA_ERR_INVALID_ARG, _lib.PA_ERR_WORKSPACE
+    P = ctypes.c_void_p
+    fake = P(256)  # never dereferenced: every call below fails its host-side checks first
+    b = _lib.pa_balls(16, 1000, 1000)
+    assert lib.pa_spatial_order(None, fake, fake, 1 << 20, None) == E
+    assert lib.pa_spatial_order(ctypes.byref(_lib.pa_balls(16, 1000, 998)), fake, fake, 1 << 20, None) == E
+    assert lib.pa_spatial_order(ctypes.byref(b), None, fake, 1 << 20, None) == E
+    assert lib.pa_spatial_order(ctypes.byref(b), fake, fake, 16, None) == W
+    assert lib.pa_spatial_order(ctypes.byref(b), fake, P(256 + 16), 1 << 20, None) == W
+    assert lib.pa_spatial_order_workspace_size(0) == 0
+    assert lib.pa_spatial_order_workspace_size(1000) > 16 * 1000
+    assert lib.pa_gather_rows(fake, P(512), 10, 8, 5, fake, None) == E  # stride < n
+    assert lib.pa_gather_rows(fake, fake, 10, 12, 5, fake, None) == E   # in == out
+    assert lib.pa_gather_rows(None, P(512), 10, 12, 5, fake, None) == E
+
+
 def test_adjoint_workspace_checked_on_host(lib):
     from paper_2412_03898_gb300 import _lib
     W = _lib.PA_ERR_WORKSPACE
