@@ -164,7 +164,8 @@ PA_API const char *pa_status_string(int32_t status);
  * pa_adjoint_4d) and pa_measure_unit_rates, changed pa_forward_batched and
  * pa_adjoint_batched to take a plan in place of a tile array, and
  * pa_batched_workspace_size to take the scenes and the plan.  2.01 gave
- * pa_adjoint an optional work-queue workspace. */
+ * pa_adjoint an optional work-queue workspace; 2.02 added pa_spatial_order
+ * and pa_gather_rows. */
 PA_API int32_t pa_version(void);
 
 /* Reads, returns in *out (host) and clears the device error word of the

@@ -353,7 +353,7 @@ const char *pa_status_string(int32_t status) {
   }
 }
 
-int32_t pa_version(void) { return 201; }
+int32_t pa_version(void) { return 202; }
 
 int32_t pa_device_error(void *stream, int32_t *out) {
   if (out == nullptr) return PA_ERR_INVALID_ARG;
