@@ -27,7 +27,7 @@ __all__ = [
     "PAProject", "PAProject4D", "PALoss", "Scene", "forward_batched", "adjoint_batched", "adam_step_scheduled", "step_increment",
     "Plan", "forward_4d", "adjoint_4d", "forward_4d_workspace_size", "adjoint_4d_workspace_size", "Buffers4D",
     "forward_plan_for",
-    "Grid", "ubp_filter", "ubp", "splat", "maps", "ssim", "measure_unit_rates",
+    "Grid", "ubp_filter", "ubp", "splat", "maps", "ssim", "measure_unit_rates", "spatial_order", "gather_rows",
 ]
 
 
