@@ -71,10 +71,13 @@ __device__ __forceinline__ FwdSmem fwd_smem(unsigned char *raw, int s_tile, int 
   return m;
 }
 
-// Radius class of a ball: quarter-octaves of a (the float's exponent and two
-// leading mantissa bits), modulo 16.  Balls of one class have windows whose
-// lengths differ by less than 19%.
-__device__ __forceinline__ int radius_class(float a) { return (int)((__float_as_uint(a) >> 21) & 15u); }
+// Radius class of a ball: half-octaves of a (the float's exponent and its
+// leading mantissa bit), modulo 16.  Balls of one class have windows whose
+// lengths differ by less than 41%; with the cloud in spatial order, classes
+// twice as large as quarter-octaves keep each class's balls closer in space,
+// which pays more than the closer lengths (static-100k: 1.97 against 2.02 ms
+// in Morton order, 2.08 against 2.08 ms along the tubes).
+__device__ __forceinline__ int radius_class(float a) { return (int)((__float_as_uint(a) >> 22) & 15u); }
 
 // Sweep order of one ball tile: a stable counting sort of the tile's slots by
 // radius class, slots past `cnt` last.  Sorted groups of pairs then have
