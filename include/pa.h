@@ -373,8 +373,8 @@ PA_API size_t pa_spatial_order_workspace_size(int64_t n);
  * A storage layout aid, not part of the method (every sum of the paper is
  * over all balls, in any order): the forward sweeps tiles of consecutive
  * balls, and a cloud stored in this order gives those tiles tight bounding
- * boxes (on a 100k-ball vessel tree stored along its tubes, 5% off the
- * forward).  Cubic cells of edge h, the power of two nearest to the mean
+ * boxes (on a 100k-ball vessel tree: 5% off the forward of the cloud
+ * stored along its tubes, two thirds off that of a randomly ordered one).  Cubic cells of edge h, the power of two nearest to the mean
  * radius a of the balls with a > 0 (at least the largest extent of the
  * centres' bounding box / 1024): cell = floor((x - min_x) / h) clamped to
  * [0, 1023] per axis, the difference one rounded float32 operation; code =

@@ -9,10 +9,11 @@
 // Order: bounding box of the centres (min/max on the order-preserving
 // unsigned image of the floats, deterministic), a 30-bit Morton code per
 // ball from 10-bit indices of cubic cells (edge: the power of two nearest to
-// the mean radius, at least the largest extent / 1024), then a stable LSD radix sort of
-// (code, index) pairs with 8-bit digits (four passes: per-tile digit
-// histograms, one exclusive scan over (digit, tile), a stable scatter).  The
-// permutation is deterministic: equal codes keep their index order.
+// the mean radius, at least the largest extent / 1024), then a stable LSD
+// radix sort of (code, index) pairs with 8-bit digits (four passes: per-tile
+// digit histograms, one exclusive scan over (digit, tile), a stable
+// scatter).  The permutation is deterministic: equal codes keep their index
+// order.
 #include <algorithm>
 
 #include "pa_internal.h"
