@@ -390,7 +390,9 @@ PA_API int32_t pa_spatial_order(const pa_balls *balls, int32_t *perm, void *work
 
 /* out[r * stride + i] = in[r * stride + perm[i]] for rows r < rows and
  * columns i < n (device arrays; out's padding columns are not written; in and
- * out must not be the same array). */
+ * out must not overlap: the same pointer is rejected, other overlaps are not
+ * detected).  perm: device int32 [n] with values in [0, n), e.g. from
+ * pa_spatial_order (not checked). */
 PA_API int32_t pa_gather_rows(const float *in, float *out, int64_t n, int64_t stride, int32_t rows,
                               const int32_t *perm, void *stream);
 
